@@ -1,0 +1,156 @@
+/*
+ * ttals.h - Online TT-ALS per-slice update (arXiv 2606.31061) on one B300 GPU.
+ *
+ * A stream delivers slices X_t of shape I_1 x ... x I_{n-1} along the last mode
+ * (Sec. 2.3, streaming tensor X[t] = X[t-1] (+) X_t).  The library keeps the
+ * time-t Tensor-Train decomposition {G_k[t]}_{k=1}^{n-1}, g_n[t] (Sec. 3.1,
+ * Eq. proposed-objective-slice) on the device and updates it once per slice
+ * with the single sweep of Algorithm 1.
+ *
+ * Conventions shared by every entry point:
+ *  - Slices are dense, C-order (last slice mode fastest), in device memory.
+ *  - Core k (1-based) has shape r_{k-1} x I_k x r_k, C-order, r_0 = 1; core n is
+ *    the temporal row g_n of length r_{n-1}.
+ *  - Ingest dtype F64 runs every step in FP64.  F32, F16 and BF16 ingest keep
+ *    the state in FP32, contract the slice with FP32 accumulation and run the
+ *    Gram / Cholesky / triangular-solve orthogonalisation in FP64.
+ *  - Calls that take a `cuda_stream` only enqueue work on it (NULL = legacy
+ *    default stream) and return without synchronising; device-side conditions
+ *    (non-finite slice, rank-deficient local solve handled by the Householder
+ *    path) are latched on the device and reported by the next synchronising call
+ *    (ttals_sync, ttals_step, ttals_cores, ttals_stats).
+ *  - The library owns every device buffer it allocates.  The caller owns slice
+ *    and output buffers and keeps them alive until the enqueued work that uses
+ *    them has completed on `cuda_stream`.
+ *  - No entry point falls back to the CPU.  If the CUDA device or the kernels
+ *    are unavailable, ttals_create fails with TTALS_ECUDA.
+ *  - A ttals_stream is not thread-safe; distinct streams may be used from
+ *    distinct host threads.
+ */
+#ifndef TTALS_H_
+#define TTALS_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ttals_stream ttals_stream; /* opaque, library-owned */
+
+typedef enum {
+    TTALS_F64 = 0,
+    TTALS_F32 = 1,
+    TTALS_F16 = 2,
+    TTALS_BF16 = 3
+} ttals_dtype;
+
+typedef enum {
+    TTALS_OK = 0,
+    TTALS_EINVAL = 1,     /* bad argument; nothing was enqueued                      */
+    TTALS_ENOMEM = 2,     /* device allocation failed                                */
+    TTALS_ECUDA = 3,      /* CUDA runtime error (message: ttals_last_error)          */
+    TTALS_ENONFINITE = 4, /* a pushed slice held NaN/Inf; that slice was not committed */
+    TTALS_ETIMEOUT = 5,   /* a bounded device wait gave up                           */
+    TTALS_ESTATE = 6      /* call not valid in the stream's current state            */
+} ttals_status;
+
+typedef struct {
+    ttals_dtype ingest;  /* dtype of every slice pushed to this stream (default F64)       */
+    uint64_t seed;       /* seed of the default random initial cores (default 0x5eed)     */
+    int device;          /* CUDA device ordinal (default 0)                               */
+    int qr_passes;       /* Gram/Cholesky orthogonalisation passes, 1 or 2; 0 = default
+                            (2 for F64 ingest, 1 otherwise)                               */
+    int reserved[4];     /* must be zero                                                  */
+} ttals_config;
+
+/*
+ * ttals_create - allocate a stream of order n = n_slice_modes + 1.
+ *   dims[0..n_slice_modes-1]  = I_1..I_{n-1} (each >= 1)
+ *   ranks[0..n_slice_modes-1] = requested TT ranks r_1..r_{n-1} (each >= 1)
+ *   cfg may be NULL (defaults).  n_slice_modes must be in [2, 8].
+ * The ranks are clamped to the feasible set r_k <= min(r_{k-1} I_k, I_{k+1} r_{k+1})
+ * (r_0 = 1) that the LQ of Sec. 3.4.1 and the QR of Sec. 3.4.2 require;
+ * ttals_effective_ranks reports the result.  The initial cores are random
+ * ("Initialize orthogonal cores randomly", Algorithm 1): Gaussian entries from a
+ * SplitMix64 / Box-Muller generator seeded with cfg->seed.  Allocates every
+ * device buffer the update needs; no later call allocates.
+ * Errors: EINVAL (shape, dtype, reserved fields), ENOMEM, ECUDA.  On error *out is NULL.
+ */
+ttals_status ttals_create(int n_slice_modes, const int64_t *dims, const int64_t *ranks,
+                          const ttals_config *cfg, ttals_stream **out);
+
+/* Release every resource of the stream (synchronises with its pending work).  NULL is a no-op. */
+void ttals_destroy(ttals_stream *s);
+
+/* Write the clamped ranks r_1..r_{n-1} to ranks_out (n_slice_modes entries). */
+ttals_status ttals_effective_ranks(const ttals_stream *s, int64_t *ranks_out);
+
+/*
+ * ttals_set_cores - replace the state by host FP64 cores (initial state or resume).
+ *   cores[k] (k = 0..n-2) points to r_k x I_{k+1} x r_{k+1} doubles (C-order, clamped
+ *   ranks), g points to r_{n-1} doubles, t is the committed step count to report.
+ * The cores need not be orthogonal: Algorithm 1 re-orthogonalises them at the next
+ * push.  Synchronous.  Clears latched errors.  Errors: EINVAL, ECUDA.
+ */
+ttals_status ttals_set_cores(ttals_stream *s, const double *const *cores, const double *g,
+                             int64_t t);
+
+/*
+ * ttals_push_slice - one step of Algorithm 1 (Sec. 3.4) for the slice X_t.
+ *   slice_dev: device pointer to prod(I_k) elements of `dtype` (C-order), 16-byte aligned.
+ *   dtype must equal the stream's ingest dtype.
+ * Enqueues the whole update on cuda_stream and returns.  If the slice holds a
+ * non-finite value the state is left unchanged and TTALS_ENONFINITE is latched.
+ * Errors returned immediately: EINVAL (NULL/misaligned pointer, dtype mismatch), ECUDA.
+ */
+ttals_status ttals_push_slice(ttals_stream *s, const void *slice_dev, ttals_dtype dtype,
+                              void *cuda_stream);
+
+/*
+ * ttals_reconstruct - write x^_t = G_1 x ... x G_{n-1} x g_n (the time-t
+ * reconstruction of the last committed slice, Sec. 3.1) to out_dev as prod(I_k)
+ * elements of out_dtype, C-order.  Asynchronous on cuda_stream.
+ * Errors: EINVAL (NULL/misaligned pointer, bad dtype), ECUDA.
+ */
+ttals_status ttals_reconstruct(ttals_stream *s, void *out_dev, ttals_dtype out_dtype,
+                               void *cuda_stream);
+
+/*
+ * ttals_cores - copy core k (1..n-1, shape r_{k-1} x I_k x r_k) or, for k = n, the
+ * temporal row g_n (r_{n-1}) of the current decomposition to host_out as doubles.
+ * n_elems must equal the core's element count.  The cores are left-orthogonal
+ * (Sec. 2.4) after at least one push.  Synchronising.
+ * Errors: EINVAL, ECUDA, plus any latched device error (the copy is still made).
+ */
+ttals_status ttals_cores(ttals_stream *s, int k, double *host_out, size_t n_elems);
+
+/*
+ * ttals_stats - per-slice accuracy of the last committed step and running totals
+ * (RE over the entire stream, Sec. 5.1).  out[0] = ||x_t||^2, out[1] = ||x_t - x^_t||^2,
+ * out[2] = sum_t ||x_t||^2, out[3] = sum_t ||x_t - x^_t||^2 over committed steps.
+ * Synchronising.  Errors: EINVAL, ECUDA, plus any latched device error.
+ */
+ttals_status ttals_stats(ttals_stream *s, double out[4]);
+
+/* ttals_step - committed step count t (synchronising; reports latched errors). */
+ttals_status ttals_step(ttals_stream *s, int64_t *t_out);
+
+/* ttals_sync - wait for the stream's enqueued work; return and clear the latched error. */
+ttals_status ttals_sync(ttals_stream *s);
+
+/* Bytes of device memory the stream holds (state + scratch); for admission control. */
+size_t ttals_device_bytes(const ttals_stream *s);
+
+/* Static text for a status code. */
+const char *ttals_status_string(ttals_status st);
+
+/* Message of the last CUDA error seen on this thread ("" if none). */
+const char *ttals_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TTALS_H_ */
