@@ -1,0 +1,411 @@
+#!/usr/bin/env python
+"""Online TT-ALS per-slice update benchmark (arXiv 2606.31061, Algorithm 1).
+
+Workload: the video-shaped 4th-order stream, 1080 x 1920 x 3 slices of uint8-range
+values (smooth TT field of ranks (32,32,3) plus integer noise, clipped to 0..255),
+method ranks (32,32,3) clamped to (32,9,3), FP16 ingest (exact for 8-bit pixels) with
+FP32 accumulation; FP32 ingest is timed alongside.  A step is one push of one slice
+through the whole update.  Synthetic, seeded frames (synth.make_stream("video")): a
+pool of 64 consecutive frames (796 MB in FP16, larger than the 126 MB L2) is played
+forward and backward so that consecutive steps stay temporally smooth.
+
+  python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+
+Prints one JSON line (rank 0).  Under torchrun each rank runs an independent replica
+stream on its own GPU (streams are independent: no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Online TT-ALS slices/s & HBM GB/s vs peak; p50/p99 per-slice latency"
+DIMS = (1080, 1920, 3)
+RANKS = (32, 32, 3)
+WORKLOAD = "video 1080x1920x3 stream, TT ranks (32,32,3) clamped to (32,9,3), T=600-step recipe"
+
+
+def env_int(name, default):
+    try:
+        return int(os.environ.get(name, default))
+    except ValueError:
+        return default
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "of measured"
+    except Exception:
+        return 6400.0, "of fallback"
+
+
+def pingpong(t, n):
+    if n == 1:
+        return 0
+    p = 2 * (n - 1)
+    u = t % p
+    return u if u < n else p - u
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 100 ms while running."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.lines = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            threading.Thread(target=self._read, daemon=True).start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append((time.time(), line.strip()))
+
+    def stop(self, t0, t1):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+        rows = [l for (ts, l) in self.lines if t0 - 0.15 <= ts <= t1 + 0.15] or [l for _, l in self.lines]
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in rows:
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1].split()[0]))
+                mx.append(float(f[2].split()[0]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def make_pool(ingest, n):
+    from paper_2606_31061_b300 import synth
+    sp = synth.make_stream("video")
+    frames = []
+    for x in sp.frames(n):
+        payload, _ = synth.round_to_ingest(x, ingest)
+        frames.append(payload)
+    return np.stack(frames)
+
+
+def to_device(pool_np, ingest):
+    import torch
+    t = torch.from_numpy(pool_np)
+    if ingest == "f16":
+        t = t.view(torch.float16)
+    elif ingest == "bf16":
+        t = t.view(torch.bfloat16)
+    return t.cuda()
+
+
+def traffic_record(kernel):
+    """DRAM bytes per launch from a committed ncu capture, if the kernel sources are unchanged."""
+    try:
+        import hashlib
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            rec = json.load(f)
+        h = hashlib.sha256()
+        src = os.path.join(ROOT, "paper_2606_31061_b300", "csrc")
+        for name in sorted(os.listdir(src)):
+            if name.endswith((".cu", ".cuh")):
+                h.update(open(os.path.join(src, name), "rb").read())
+        r = rec.get(kernel)
+        if r and r.get("src_sha256") == h.hexdigest():
+            return r.get("bytes_per_launch")
+    except Exception:
+        pass
+    return None
+
+
+def time_arm(ingest, steps, warmup, pool, dist_on, sampler_idx):
+    """Device-timed throughput of `steps` pushes; per-kernel event timing on the launch stream."""
+    import torch
+    from paper_2606_31061_b300.ttals import Stream
+    st = Stream(DIMS, RANKS, ingest=ingest)
+    P = pool.shape[0]
+    stream = torch.cuda.current_stream()
+    h = stream.cuda_stream
+    for t in range(warmup):
+        st.push_ptr(pool[pingpong(t, P)].data_ptr(), h)
+    torch.cuda.synchronize()
+    if dist_on:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize()
+    st.profile(True)
+    n0 = st.launch_count
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    clocks = None
+    sampler = ClockSampler(sampler_idx) if sampler_idx is not None else None
+    if sampler:
+        sampler.start()
+        time.sleep(0.3)
+    w0 = time.time()
+    e0.record(stream)
+    for t in range(steps):
+        st.push_ptr(pool[pingpong(warmup + t, P)].data_ptr(), h)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    w1 = time.time()
+    if dist_on:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize()
+    if sampler:
+        clocks = sampler.stop(w0, w1)
+    ms = e0.elapsed_time(e1)
+    launches = st.launch_count - n0
+    ms_solve, ms_env, ms_push, npush = st.profile_read()
+    st.profile(False)
+    # per-slice latency distribution: one event pair per push, measured separately so the
+    # per-push event records do not sit inside the throughput region above
+    lat = []
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(min(steps, 400))]
+    for t, (a, b) in enumerate(ev):
+        a.record(stream)
+        st.push_ptr(pool[pingpong(warmup + steps + t, P)].data_ptr(), h)
+        b.record(stream)
+    torch.cuda.synchronize()
+    lat = sorted(a.elapsed_time(b) for a, b in ev)
+    stats = st.stats()
+    st.close()
+    return dict(ms=ms, launches=launches, ms_solve=ms_solve, ms_env=ms_env, ms_push=ms_push, npush=npush,
+                lat=lat, clocks=clocks, re=math.sqrt(stats[3] / stats[2]) if stats[2] > 0 else None)
+
+
+def e2e_arm(ingest, steps, pool_np, dist_on):
+    """Same metric through the C ABI from pinned HOST buffers: per step an H2D copy of the
+    slice (copy stream, double-buffered device slot), the push, and an async D2H read of
+    the step's error statistics.  Copies overlap the previous step's update."""
+    import torch
+    from paper_2606_31061_b300.ttals import Stream
+    st = Stream(DIMS, RANKS, ingest=ingest)
+    P = min(16, pool_np.shape[0])
+    host = torch.from_numpy(pool_np[:P]).pin_memory()
+    slot_shape = host.shape[1:]
+    dev = [torch.empty(slot_shape, dtype=host.dtype, device="cuda") for _ in range(2)]
+    out = torch.zeros((steps, 4), dtype=torch.float64).pin_memory()
+    comp = torch.cuda.current_stream()
+    copy = torch.cuda.Stream()
+    copied = [torch.cuda.Event() for _ in range(2)]
+    consumed = [torch.cuda.Event() for _ in range(2)]
+    for i in range(2):
+        consumed[i].record(comp)
+
+    def one(t):
+        s = t % 2
+        with torch.cuda.stream(copy):
+            copy.wait_event(consumed[s])
+            dev[s].copy_(host[pingpong(t, P)], non_blocking=True)
+            copied[s].record(copy)
+        comp.wait_event(copied[s])
+        st.push_ptr(dev[s].data_ptr(), comp.cuda_stream)
+        consumed[s].record(comp)
+        st.stats_async(out[t].data_ptr(), comp.cuda_stream)
+
+    for t in range(min(3, steps)):
+        one(t)
+    torch.cuda.synchronize()
+    if dist_on:
+        import torch.distributed as dist
+        dist.barrier()
+    t0 = time.perf_counter()
+    for t in range(steps):
+        one(t)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    st.close()
+    slice_bytes = int(np.prod(DIMS)) * host.element_size()
+    return dict(seconds=t1 - t0, h2d=slice_bytes, d2h=4 * 8)
+
+
+def cpu_baseline_oracle(ingest, budget_s=15.0, max_steps=None):
+    """The FP64 oracle (test infrastructure) on the host cores, on a bounded prefix of the
+    same stream: returns (slices/s, steps, threads, seconds)."""
+    from oracle import ttals_oracle as O
+    from paper_2606_31061_b300 import synth
+    try:
+        from threadpoolctl import threadpool_info
+        threads = max([d.get("num_threads", 1) for d in threadpool_info()] + [1])
+    except Exception:
+        threads = os.cpu_count() or 1
+    sp = synth.make_stream("video")
+    r = O.clamp_ranks(DIMS, RANKS)
+    cores, g = synth.init_cores(DIMS, r, seed=7)
+    orc = O.OnlineTTALS(DIMS, r, cores, g)
+    gen = sp.frames(10_000)
+    done, spent = 0, 0.0
+    while spent < budget_s and (max_steps is None or done < max_steps):
+        x = next(gen)
+        _, exact = synth.round_to_ingest(x, ingest)
+        a = time.perf_counter()
+        orc.step(exact)
+        spent += time.perf_counter() - a
+        done += 1
+    return done / spent, done, threads, spent
+
+
+def run_reference(args, rank):
+    if rank != 0:
+        return
+    budget = 120.0
+    rate, done, threads, spent = cpu_baseline_oracle(args.ingest, budget_s=budget,
+                                                     max_steps=max(1, args.steps))
+    line = {
+        "impl": "reference", "metric": METRIC, "value": rate, "unit": "slices/s", "n_gpus": args.gpus,
+        "steps": done, "warmup": 0, "ms_per_step": 1000.0 / rate, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "ingest": args.ingest, "parallelism": "host cores"},
+        "cpu_baseline": {"value": rate, "unit": "slices/s", "cores": threads, "kind": "oracle",
+                         "sample": f"first {done} frames of the stream (of {args.steps} requested; "
+                                   f"capped at {budget:.0f} s of oracle time), FP64 literal Algorithm 1"},
+        "e2e": {"value": rate, "unit": "slices/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=50)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--ingest", default="f16", choices=["f16", "f32", "bf16"])
+    ap.add_argument("--pool", type=int, default=64)
+    ap.add_argument("--no-f32", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=300)
+    args = ap.parse_args()
+    rank = env_int("RANK", 0)
+    world = env_int("WORLD_SIZE", 1)
+    local = env_int("LOCAL_RANK", 0)
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+    if args.warmup < 3:
+        args.warmup = 3
+    import torch
+    torch.cuda.set_device(local)
+    dist_on = world > 1
+    if dist_on:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2606_31061_b300 import build
+    if rank == 0 or not dist_on:
+        build.build()
+    if dist_on:
+        torch.distributed.barrier()
+    pool_np = make_pool(args.ingest, args.pool)
+    pool = to_device(pool_np, args.ingest)
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    smi_idx = int(vis.split(",")[local]) if vis else local
+    r = time_arm(args.ingest, args.steps, args.warmup, pool, dist_on, smi_idx if rank == 0 else None)
+    sec = r["ms"] / 1000.0
+    if dist_on:
+        t = torch.tensor([sec], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        sec = float(t.item())
+    value = args.steps * world / sec
+    slice_bytes = int(np.prod(DIMS)) * pool.element_size()
+    r1, rest1, i1 = 32, 1920 * 3, 1080
+    alg = {"solve": slice_bytes + r1 * rest1 * 4 + i1 * r1 * 4,
+           "env": slice_bytes + i1 * r1 * 4 + r1 * rest1 * 4}
+    per = {"solve": r["ms_solve"] / max(1, r["npush"]), "env": r["ms_env"] / max(1, r["npush"])}
+    dom = max(per, key=per.get)
+    peak, peak_src = peaks()
+    achieved = alg[dom] / (per[dom] * 1e-3) / 1e9
+    kname = {"solve": "level-1 local solve Y = X_(1) B^_1^T", "env": "level-1 environment E_2 = G_1^T X_(1)"}[dom]
+    e2e = e2e_arm(args.ingest, args.e2e_steps, pool_np, dist_on)
+    e2e_sec = e2e["seconds"]
+    if dist_on:
+        t = torch.tensor([e2e_sec], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_sec = float(t.item())
+    f32 = None
+    if not args.no_f32 and args.ingest != "f32":
+        del pool
+        torch.cuda.empty_cache()
+        pool32_np = make_pool("f32", min(args.pool, 48))
+        pool32 = to_device(pool32_np, "f32")
+        r32 = time_arm("f32", args.steps, args.warmup, pool32, dist_on, None)
+        f32 = {"value": args.steps * world / (r32["ms"] / 1000.0), "unit": "slices/s",
+               "ms_per_step": r32["ms"] / args.steps, "re": r32["re"],
+               "hbm_gbs": args.steps * world / (r32["ms"] / 1000.0) * int(np.prod(DIMS)) * 4 / 1e9}
+        del pool32
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rate, done, threads, spent = cpu_baseline_oracle(args.ingest, budget_s=15.0)
+        cpu = {"value": rate, "unit": "slices/s", "cores": threads, "kind": "oracle",
+               "sample": f"first {done} frames of the same stream ({spent:.1f} s), FP64 literal Algorithm 1"}
+    lat = r["lat"]
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "slices/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": r["ms"] / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": args.ingest, "data": "synthetic",
+            "config": {"workload": WORKLOAD, "ingest": args.ingest,
+                       "precision": f"{args.ingest.upper()} ingest, FP32 accumulation and state, "
+                                    "FP32 Cholesky factor + FP64 polar re-orthogonalisation",
+                       "l2": f"inputs larger than L2: {args.pool}-frame pool "
+                             f"({args.pool * slice_bytes / 1e6:.0f} MB), played forward and backward",
+                       "parallelism": f"replicas x{world}" if world > 1 else "single stream"},
+            "hbm_gbs": value * slice_bytes / 1e9,
+            "latency_ms": {"p50": lat[len(lat) // 2], "p99": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
+                           "n": len(lat)},
+            "re": r["re"],
+            "roofline": {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": peak,
+                         "peak_source": peak_src, "unit": "GB/s", "frac": achieved / peak,
+                         "traffic": traffic_record(dom),
+                         "algorithmic_bytes": alg[dom], "ms_per_launch": per[dom],
+                         "step_share": per[dom] / (r["ms_push"] / max(1, r["npush"]))},
+            "e2e": {"value": args.e2e_steps * world / e2e_sec, "unit": "slices/s",
+                    "h2d_bytes_per_step": e2e["h2d"], "d2h_bytes_per_step": e2e["d2h"]},
+            "gpu_launches": r["launches"],
+            "clocks": r["clocks"],
+            "f32_ingest": f32,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    if dist_on:
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

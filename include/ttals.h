@@ -12,8 +12,9 @@
  *  - Core k (1-based) has shape r_{k-1} x I_k x r_k, C-order, r_0 = 1; core n is
  *    the temporal row g_n of length r_{n-1}.
  *  - Ingest dtype F64 runs every step in FP64.  F32, F16 and BF16 ingest keep
- *    the state in FP32, contract the slice with FP32 accumulation and run the
- *    Gram / Cholesky / triangular-solve orthogonalisation in FP64.
+ *    the state in FP32 and contract the slice with FP32 accumulation; each local
+ *    solve is orthogonalised by a Gram / Cholesky pass (FP32 factor, FP64 sums)
+ *    followed by one FP64 polar re-orthogonalisation.
  *  - Calls that take a `cuda_stream` only enqueue work on it (NULL = legacy
  *    default stream) and return without synchronising; device-side conditions
  *    (non-finite slice, rank-deficient local solve handled by the Householder
@@ -60,8 +61,9 @@ typedef struct {
     ttals_dtype ingest;  /* dtype of every slice pushed to this stream (default F64)       */
     uint64_t seed;       /* seed of the default random initial cores (default 0x5eed)     */
     int device;          /* CUDA device ordinal (default 0)                               */
-    int qr_passes;       /* Gram/Cholesky orthogonalisation passes, 1 or 2; 0 = default
-                            (2 for F64 ingest, 1 otherwise)                               */
+    int qr_passes;       /* orthogonalisation passes per local solve: 1 = Cholesky-QR with an
+                            FP32 factor only, 2 = followed by one FP64 polar
+                            re-orthogonalisation (0 = default = 2)                        */
     int reserved[4];     /* must be zero                                                  */
 } ttals_config;
 
@@ -142,6 +144,26 @@ ttals_status ttals_sync(ttals_stream *s);
 
 /* Bytes of device memory the stream holds (state + scratch); for admission control. */
 size_t ttals_device_bytes(const ttals_stream *s);
+
+/*
+ * Instrumentation (the paper has no counterpart; tracing and metrics of the library).
+ *
+ * ttals_launch_count - number of CUDA kernels this stream has launched so far
+ *   (a host-side counter; no synchronisation).
+ * ttals_stats_async - enqueue on cuda_stream a copy of the four ttals_stats values
+ *   {||x_t||^2, ||x_t - x^_t||^2, sum ||x||^2, sum ||x - x^||^2} into out4 (host
+ *   pinned or device memory, 4 doubles).  Errors: EINVAL, ECUDA.
+ * ttals_profile - enable (1) or disable (0) per-push timing: CUDA events recorded on
+ *   the launch stream around the whole update and around the level-1 local solve
+ *   Y = X_(1) B_1^T and the level-1 environment E_2 = G_1^T X_(1).  Synchronising.
+ * ttals_profile_read - wait, then write the summed milliseconds over the pushes timed
+ *   since the last read: ms_out[0] level-1 solve, ms_out[1] level-1 environment,
+ *   ms_out[2] whole update; *n_out = number of pushes.  Resets the totals.
+ */
+uint64_t ttals_launch_count(const ttals_stream *s);
+ttals_status ttals_stats_async(ttals_stream *s, double *out4, void *cuda_stream);
+ttals_status ttals_profile(ttals_stream *s, int enable);
+ttals_status ttals_profile_read(ttals_stream *s, double ms_out[3], int64_t *n_out);
 
 /* Static text for a status code. */
 const char *ttals_status_string(ttals_status st);

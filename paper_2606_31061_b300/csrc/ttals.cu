@@ -1,0 +1,811 @@
+// ttals.cu - C ABI and per-slice orchestration of the Online TT-ALS update
+// (arXiv 2606.31061, Algorithm 1) on one GPU.
+//
+// Gauge-reduced form of Algorithm 1.  x^_t (and the left-orthogonal cores it is
+// built from) depends on the right interfaces B_k only through their row spaces:
+// the LQ sweep of Sec. 3.4.1 gives B_k = L_{k+1}^{-1} B^_k with
+// B^_k = G_{k+1} x ... x G_{n-1} x g_n, and L_{k+1} is invertible for generic
+// data, so QR(E_k B_k^T) and QR(E_k B^_k^T) span the same space and produce the
+// same A_{k+1} up to an r x r orthogonal gauge.  The device therefore skips the
+// LQ sweep and uses B^_k directly.
+//
+// Saturation.  Let k* be the first level with r_k >= I_{k+1}...I_{n-1} (it exists:
+// r_{n-1} >= 1).  From k* on the clamped ranks span every vector of the trailing
+// modes, so x^_t = A_{k*} E_{k*} with E_{k*} = A_{k*}^T X_t.  The device keeps the
+// cores G_1..G_{k*-1} and C = E_{k*} (the contraction G_{k*} x ... x g_n) and
+// materialises G_{k*}..G_{n-1}, g_n only when they are read (ttals_cores).
+// For the 3rd-order and video-shaped streams k* = 2 and one step is
+//   Y = X_(1) C^T,  G_1 = orth(Y),  C = G_1^T X_(1).
+#include "ttals.h"
+#include "ttals_kernels.cuh"
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <string>
+#include <type_traits>
+#include <vector>
+
+using namespace ttals;
+
+namespace {
+
+thread_local std::string g_last_err;
+
+#define TT_CUDA(x)                                                      \
+  do {                                                                  \
+    cudaError_t e_ = (x);                                               \
+    if (e_ != cudaSuccess) {                                            \
+      g_last_err = std::string(#x) + ": " + cudaGetErrorString(e_);    \
+      return TTALS_ECUDA;                                               \
+    }                                                                   \
+  } while (0)
+
+#define TT_TRY(x)                        \
+  do {                                   \
+    ttals_status s_ = (x);               \
+    if (s_ != TTALS_OK) return s_;       \
+  } while (0)
+
+constexpr int kSMs = 148;
+
+inline long long cdiv(long long a, long long b) { return (a + b - 1) / b; }
+
+// split-K choice for the generic GEMM: enough CTAs for ~2 waves on 148 SMs
+struct GemmShape {
+  int M, N;
+  long long K;
+  int nsplit;
+  long long kchunk;
+  dim3 grid;
+};
+
+GemmShape plan_gemm(int M, int N, long long K, bool allow_split) {
+  GemmShape g;
+  g.M = M;
+  g.N = N;
+  g.K = K;
+  const long long tiles = cdiv(M, GB_M) * cdiv(N, GB_N);
+  long long ns = allow_split ? std::max<long long>(1, cdiv(2 * kSMs, tiles)) : 1;
+  ns = std::min<long long>(ns, std::max<long long>(1, cdiv(K, GB_K)));
+  ns = std::min<long long>(ns, 64);
+  long long kc = cdiv(cdiv(K, ns), GB_K) * GB_K;
+  if (kc < GB_K) kc = GB_K;
+  g.kchunk = kc;
+  g.nsplit = (int)std::max<long long>(1, cdiv(K, kc));
+  g.grid = dim3((unsigned)cdiv(M, GB_M), (unsigned)cdiv(N, GB_N), (unsigned)g.nsplit);
+  return g;
+}
+
+// SplitMix64 (Steele, Lea & Flood 2014) and Box-Muller for the default initial cores
+struct SplitMix64 {
+  uint64_t s;
+  uint64_t next() {
+    uint64_t z = (s += 0x9E3779B97F4A7C15ull);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+  }
+  double uniform() { return ((next() >> 11) + 0.5) * (1.0 / 9007199254740992.0); }
+  double gauss() {
+    const double u1 = uniform(), u2 = uniform();
+    return std::sqrt(-2.0 * std::log(u1)) * std::cos(6.283185307179586 * u2);
+  }
+};
+
+size_t dtype_size(ttals_dtype d) {
+  switch (d) {
+    case TTALS_F64: return 8;
+    case TTALS_F32: return 4;
+    case TTALS_F16: return 2;
+    case TTALS_BF16: return 2;
+  }
+  return 0;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// stream object
+// ---------------------------------------------------------------------------
+struct ttals_stream {
+  int m = 0;                          // n - 1 slice modes
+  std::vector<long long> dims;        // I_1..I_m
+  std::vector<long long> full;        // r_0..r_m (r_0 = 1)
+  std::vector<long long> rest;        // rest[k] = I_{k+1}...I_m (rest[m] = 1)
+  int kstar = 1;
+  ttals_dtype ingest = TTALS_F64;
+  int device = 0;
+  int qr_passes = 1;
+  cudaStream_t last = nullptr;
+  bool have_last = false;
+  cudaEvent_t ev = nullptr;
+  Ctl* ctl = nullptr;
+  size_t bytes = 0;
+  std::vector<void*> allocs;
+  unsigned long long nlaunch = 0;      // kernels launched by this stream (host counter)
+  // optional timing of the level-1 kernels: CUDA events recorded on the launch stream
+  bool profiling = false;
+  std::vector<cudaEvent_t> ev_pool;    // recorded events, in groups of kProfEvents per push
+  size_t ev_used = 0;
+  static constexpr int kProfEvents = 6; // push begin, solve1 begin/end, env1 begin/end, push end
+
+  virtual ~ttals_stream() {
+    if (have_last) cudaStreamSynchronize(last);
+    for (void* p : allocs) cudaFree(p);
+    for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);
+    if (ev) cudaEventDestroy(ev);
+  }
+  // event slot `i` of the current push (profiling only)
+  ttals_status mark(int i, cudaStream_t s) {
+    if (!profiling) return TTALS_OK;
+    const size_t idx = ev_used + (size_t)i;
+    while (ev_pool.size() <= idx) {
+      cudaEvent_t e;
+      TT_CUDA(cudaEventCreate(&e));
+      ev_pool.push_back(e);
+    }
+    TT_CUDA(cudaEventRecord(ev_pool[idx], s));
+    return TTALS_OK;
+  }
+  virtual ttals_status push(const void* x, cudaStream_t s) = 0;
+  virtual ttals_status reconstruct(void* out, ttals_dtype dt, cudaStream_t s) = 0;
+  virtual ttals_status set_cores(const double* const* cores, const double* g, long long t) = 0;
+  virtual ttals_status get_core(int k, double* host, size_t n) = 0;
+  virtual ttals_status allocate() = 0;
+
+  long long slice_elems() const { return rest[0]; }
+  long long core_elems(int k) const {   // k = 1..m
+    return full[k - 1] * dims[k - 1] * full[k];
+  }
+
+  template <typename T>
+  ttals_status dalloc(T** p, size_t n) {
+    *p = nullptr;
+    if (n == 0) n = 1;
+    cudaError_t e = cudaMalloc((void**)p, n * sizeof(T));
+    if (e != cudaSuccess) {
+      g_last_err = std::string("cudaMalloc: ") + cudaGetErrorString(e);
+      cudaGetLastError();
+      return e == cudaErrorMemoryAllocation ? TTALS_ENOMEM : TTALS_ECUDA;
+    }
+    allocs.push_back((void*)*p);
+    bytes += n * sizeof(T);
+    return TTALS_OK;
+  }
+
+  ttals_status order_after_last(cudaStream_t s) {
+    if (have_last && s != last) {
+      TT_CUDA(cudaEventRecord(ev, last));
+      TT_CUDA(cudaStreamWaitEvent(s, ev, 0));
+    }
+    last = s;
+    have_last = true;
+    return TTALS_OK;
+  }
+
+  ttals_status sync_and_read(Ctl* h, bool clear) {
+    if (have_last) TT_CUDA(cudaStreamSynchronize(last));
+    TT_CUDA(cudaMemcpy(h, ctl, sizeof(Ctl), cudaMemcpyDeviceToHost));
+    if (clear && h->latched) {
+      int zero = 0;
+      TT_CUDA(cudaMemcpy(&ctl->latched, &zero, sizeof(int), cudaMemcpyHostToDevice));
+    }
+    return TTALS_OK;
+  }
+};
+
+namespace {
+
+template <typename TX, typename TC>
+struct Impl final : ttals_stream {
+  using TG = TC;                       // per-CTA Gram accumulation type
+  // state, double-buffered by parity
+  TC* G[2][kMaxLevels] = {};
+  TC* C[2] = {};
+  int par = 0;
+  // scratch
+  TC* Bhat[kMaxLevels] = {};           // B^_k, k = 1..k*-2 (also reconstruct temporaries)
+  TC* E[kMaxLevels + 1] = {};          // E_k, k = 2..k*-1
+  TC* part = nullptr;                  // split-K partials
+  TC* Y = nullptr;                     // reduced local-solve matrix of a level
+  TC* Qa = nullptr;                    // first-pass orthogonal factor
+  double* Wpart = nullptr;
+  double* T64 = nullptr;
+  float* T32 = nullptr;
+  double* sumsq = nullptr;
+  double* ccpart = nullptr;
+  double* hh = nullptr;                // Householder work (fallback and materialisation)
+  double* dcores = nullptr;            // FP64 staging of all cores (set_cores)
+  double* dtmp[2] = {};                // FP64 chain temporaries (size of C)
+  double* mat_q[kMaxLevels + 1] = {};  // materialised cores k*..m (FP64)
+  double* mat_g = nullptr;             // materialised g_n
+  double* dout = nullptr;              // FP64 staging for core readout
+  bool materialised = false;
+  size_t part_elems = 0, y_elems = 0, wpart_elems = 0, sumsq_elems = 0, cc_elems = 0, hh_elems = 0;
+
+  int rows(int k) const { return (int)(full[k - 1] * dims[k - 1]); }  // r_{k-1} I_k
+  int rk(int k) const { return (int)full[k]; }
+
+  GemmShape plan_solve(int k) const {      // Y = E_k B^_k^T
+    return plan_gemm(rows(k), rk(k), rest[k], true);
+  }
+  GemmShape plan_env(int k) const {        // E_{k+1}^T = E_k^T Q_k
+    return plan_gemm((int)rest[k], rk(k), rows(k), true);
+  }
+  int gram_blocks(long long nrows) const { return (int)std::min<long long>(64, cdiv(nrows, 16)); }
+
+  ttals_status allocate() override {
+    const bool f64 = std::is_same<TC, double>::value;
+    (void)f64;
+    for (int p = 0; p < 2; ++p) {
+      for (int k = 1; k < kstar; ++k) TT_TRY(dalloc(&G[p][k - 1], (size_t)core_elems(k)));
+      TT_TRY(dalloc(&C[p], (size_t)(full[kstar - 1] * rest[kstar - 1])));
+    }
+    for (int k = 1; k + 1 < kstar; ++k) TT_TRY(dalloc(&Bhat[k], (size_t)(full[k] * rest[k])));
+    for (int k = 2; k < kstar; ++k) TT_TRY(dalloc(&E[k], (size_t)(full[k - 1] * rest[k - 1])));
+    // reconstruct temporaries need r_{k-1} x rest_{k-1} for k = 2..k*-1: Bhat[k-1] has it
+    for (int k = 1; k < kstar; ++k) {
+      GemmShape a = plan_solve(k), b = plan_env(k);
+      part_elems = std::max<size_t>(part_elems, (size_t)a.nsplit * a.M * a.N);
+      part_elems = std::max<size_t>(part_elems, (size_t)b.nsplit * b.M * b.N);
+      y_elems = std::max<size_t>(y_elems, (size_t)rows(k) * rk(k));
+      wpart_elems = std::max<size_t>(wpart_elems, (size_t)gram_blocks(rows(k)) * rk(k) * rk(k));
+      cc_elems = std::max<size_t>(cc_elems, (size_t)kSMs * 4);
+      if (k == 1) sumsq_elems = (size_t)a.grid.x * a.grid.z;
+      hh_elems = std::max<size_t>(hh_elems, (size_t)2 * rows(k) * rk(k));
+    }
+    for (int k = std::max(kstar, 1); k <= m; ++k)
+      hh_elems = std::max<size_t>(hh_elems, (size_t)2 * rows(k) * std::max<long long>(rest[k], full[k]));
+    cc_elems = std::max<size_t>(cc_elems, (size_t)kSMs * 4);
+    TT_TRY(dalloc(&part, std::max<size_t>(part_elems, 1)));
+    TT_TRY(dalloc(&Y, std::max<size_t>(y_elems, 1)));
+    TT_TRY(dalloc(&Qa, std::max<size_t>(y_elems, 1)));
+    TT_TRY(dalloc(&Wpart, std::max<size_t>(wpart_elems, 1)));
+    TT_TRY(dalloc(&T64, (size_t)kMaxRank * kMaxRank));
+    TT_TRY(dalloc(&T32, (size_t)kMaxRank * kMaxRank));
+    TT_TRY(dalloc(&sumsq, std::max<size_t>(sumsq_elems, 1)));
+    TT_TRY(dalloc(&ccpart, cc_elems));
+    TT_TRY(dalloc(&hh, std::max<size_t>(hh_elems, 1)));
+    size_t ncores = 0;
+    for (int k = 1; k <= m; ++k) ncores += (size_t)core_elems(k);
+    TT_TRY(dalloc(&dcores, ncores + (size_t)full[m]));
+    const size_t csz = (size_t)(full[kstar - 1] * rest[kstar - 1]);
+    TT_TRY(dalloc(&dtmp[0], csz));
+    TT_TRY(dalloc(&dtmp[1], csz));
+    for (int k = kstar; k <= m; ++k) TT_TRY(dalloc(&mat_q[k], (size_t)core_elems(k)));
+    TT_TRY(dalloc(&mat_g, (size_t)full[m]));
+    size_t maxcore = 0;
+    for (int k = 1; k <= m; ++k) maxcore = std::max<size_t>(maxcore, (size_t)core_elems(k));
+    TT_TRY(dalloc(&dout, maxcore));
+    TT_TRY(dalloc(&ctl, 1));
+    TT_CUDA(cudaMemset(ctl, 0, sizeof(Ctl)));
+    TT_CUDA(cudaFuncSetAttribute(k_factor, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024));
+    return TTALS_OK;
+  }
+
+  // ---- launch helpers --------------------------------------------------------
+  template <typename TA, typename TB, typename TACC, typename TD, bool AK, bool BK>
+  ttals_status gemm(const GemmShape& g, const TA* A, long long lda, const TB* B, long long ldb, TD* D,
+                    long long sdm, long long sdn, long long sstride, double* ss,
+                    const double* bzero, const Ctl* chk, Ctl* reset, cudaStream_t s) {
+    k_gemm<TA, TB, TACC, TD, AK, BK><<<g.grid, G_THREADS, 0, s>>>(
+        A, lda, B, ldb, D, sdm, sdn, sstride, g.M, g.N, g.K, g.kchunk, ss, bzero, chk, reset);
+    TT_CUDA(cudaGetLastError());
+    ++nlaunch;
+    return TTALS_OK;
+  }
+
+  // orthonormal basis of the level-k local solve.  Input: split partials of Y
+  // (nsplit x rows x r) in `part`.  Output: Q (rows x r) in `qout`.
+  ttals_status orth(int k, int nsplit, bool first, TC* qout, cudaStream_t s) {
+    const long long n = rows(k);
+    const int r = rk(k);
+    const int nb = gram_blocks(n);
+    const long long rpb = cdiv(n, nb);
+    const int nblk = (int)cdiv(n, rpb);
+    const size_t gsm = (size_t)GRAM_CHUNK * r * sizeof(TG);
+    const size_t fsm = (size_t)r * r * 8 + (size_t)r * 8 + (size_t)r * (r + 1) * 4;
+    const size_t asm_ = (size_t)r * r * sizeof(TC);
+    const int ablk = (int)std::min<long long>(4 * kSMs, std::max<long long>(1, cdiv(n * r, APPLY_THREADS)));
+    const int sum_n = (int)sumsq_elems;
+    for (int pass = 0; pass < qr_passes; ++pass) {
+      const int slot = 2 * (k - 1) + pass;
+      const TC* src = pass == 0 ? (const TC*)part : (const TC*)Qa;
+      TC* dst = (pass + 1 == qr_passes) ? qout : Qa;
+      k_gram<TC, TC, TG><<<nblk, GRAM_THREADS, gsm, s>>>(src, pass == 0 ? nsplit : 1, n * r, n, r,
+                                                          pass == 0 ? Y : nullptr, Wpart, rpb, ctl);
+      TT_CUDA(cudaGetLastError());
+      k_factor<<<1, FACT_THREADS, fsm, s>>>(Wpart, nblk, r, pass == 0 ? 0 : 1, T64, T32, ctl, slot,
+                                             sumsq, sum_n, (first && pass == 0) ? 1 : 0);
+      TT_CUDA(cudaGetLastError());
+      k_apply<TC><<<ablk, APPLY_THREADS, asm_, s>>>(pass == 0 ? Y : Qa, n, r, pass == 0 ? 0 : 1, T64, T32,
+                                                     dst, ctl, slot, hh);
+      TT_CUDA(cudaGetLastError());
+      nlaunch += 3;
+    }
+    return TTALS_OK;
+  }
+
+  // ---- one step of Algorithm 1 -------------------------------------------------
+  ttals_status push(const void* xv, cudaStream_t s) override {
+    TT_TRY(mark(0, s));
+    TT_TRY(push_body(xv, s));
+    TT_TRY(mark(5, s));
+    if (profiling) ev_used += kProfEvents;
+    return TTALS_OK;
+  }
+
+  ttals_status push_body(const void* xv, cudaStream_t s) {
+    const TX* X = (const TX*)xv;
+    const int np = 1 - par;
+    materialised = false;
+    CopyList rl{};
+    for (int k = 1; k < kstar; ++k) {
+      rl.src[rl.n] = G[par][k - 1];
+      rl.dst[rl.n] = G[np][k - 1];
+      rl.bytes[rl.n] = core_elems(k) * (long long)sizeof(TC);
+      ++rl.n;
+    }
+    rl.src[rl.n] = C[par];
+    rl.dst[rl.n] = C[np];
+    rl.bytes[rl.n] = full[kstar - 1] * rest[kstar - 1] * (long long)sizeof(TC);
+    ++rl.n;
+
+    if (kstar == 1) {   // r_1 >= I_2...I_{n-1}: x^_t = X_t
+      const int nb = (int)std::min<long long>(cdiv(rest[0], 256), 2 * kSMs);
+      k_copy_slice<TX, TC><<<nb, 256, 0, s>>>(X, rest[0], C[np], ccpart, ctl);
+      TT_CUDA(cudaGetLastError());
+      k_commit<<<1, 256, 0, s>>>(ctl, ccpart, nb, ccpart, nb, rl);
+      TT_CUDA(cudaGetLastError());
+      nlaunch += 2;
+      par = np;
+      return TTALS_OK;
+    }
+    bool first_launch = true;
+    // right interfaces B^_k = G_{k+1} x B^_{k+1}, B^_{k*-1} = C  (old state)
+    for (int k = kstar - 2; k >= 1; --k) {
+      const bool fromC = (k == kstar - 2);
+      const TC* Bsrc = fromC ? C[par] : Bhat[k + 1];
+      GemmShape g = plan_gemm(rows(k + 1), (int)rest[k + 1], rk(k + 1), false);
+      TT_TRY((gemm<TC, TC, TC, TC, true, false>(g, G[par][k], rk(k + 1), Bsrc, rest[k + 1], Bhat[k], rest[k + 1],
+                                                 1, 0, nullptr, fromC ? &ctl->cc : nullptr, nullptr,
+                                                 first_launch ? ctl : nullptr, s)));
+      first_launch = false;
+    }
+    // forward sweep
+    int ncc = 0;
+    for (int k = 1; k < kstar; ++k) {
+      const bool last_level = (k == kstar - 1);
+      const TC* Bk = last_level ? C[par] : Bhat[k];
+      GemmShape gs = plan_solve(k);
+      if (k == 1) {
+        TT_TRY(mark(1, s));
+        TT_TRY(solve_level1(gs, X, Bk, last_level ? &ctl->cc : nullptr, first_launch ? ctl : nullptr, s));
+        TT_TRY(mark(2, s));
+      } else {
+        TT_TRY((gemm<TC, TC, TC, TC, true, true>(gs, E[k], rest[k], Bk, rest[k], part, rk(k), 1,
+                                                 (long long)gs.M * gs.N, nullptr,
+                                                 last_level ? &ctl->cc : nullptr, ctl, nullptr, s)));
+      }
+      first_launch = false;
+      TC* qdst = G[np][k - 1];
+      TT_TRY(orth(k, gs.nsplit, k == 1, qdst, s));
+      GemmShape ge = plan_env(k);
+      if (k == 1) {
+        TT_TRY(mark(3, s));
+        TT_TRY(env_level1(ge, X, qdst, s));
+        TT_TRY(mark(4, s));
+      } else {
+        TT_TRY((gemm<TC, TC, TC, TC, false, false>(ge, E[k], rest[k], qdst, rk(k), part, rk(k), 1,
+                                                   (long long)ge.M * ge.N, nullptr, nullptr, ctl, nullptr, s)));
+      }
+      TC* eout = last_level ? C[np] : E[k + 1];
+      const int nb = (int)std::min<long long>(cdiv(rest[k] * rk(k), RED_THREADS), 4 * kSMs);
+      k_reduce_t<TC><<<nb, RED_THREADS, 0, s>>>(part, ge.nsplit, (long long)ge.M * ge.N, rest[k], rk(k), eout,
+                                                last_level ? ccpart : nullptr, ctl);
+      TT_CUDA(cudaGetLastError());
+      ++nlaunch;
+      if (last_level) ncc = nb;
+    }
+    k_commit<<<1, 256, 0, s>>>(ctl, ccpart, ncc, nullptr, 0, rl);
+    TT_CUDA(cudaGetLastError());
+    ++nlaunch;
+    par = np;
+    return TTALS_OK;
+  }
+
+  // level-1 local solve Y = X_(1) B^_1^T (split-K partials into `part`, ||x||^2 partials)
+  ttals_status solve_level1(const GemmShape& gs, const TX* X, const TC* Bk, const double* bzero, Ctl* reset,
+                            cudaStream_t s) {
+    return gemm<TX, TC, TC, TC, true, true>(gs, X, rest[1], Bk, rest[1], part, rk(1), 1,
+                                           (long long)gs.M * gs.N, sumsq, bzero, nullptr, reset, s);
+  }
+  // level-1 environment E_2^T = X_(1)^T G_1 (split partials into `part`)
+  ttals_status env_level1(const GemmShape& ge, const TX* X, const TC* Q, cudaStream_t s) {
+    return gemm<TX, TC, TC, TC, false, false>(ge, X, rest[1], Q, rk(1), part, rk(1), 1, (long long)ge.M * ge.N,
+                                             nullptr, nullptr, ctl, nullptr, s);
+  }
+
+  // ---- x^_t = G_1 x ... x G_{k*-1} x C ------------------------------------------
+  ttals_status reconstruct(void* out, ttals_dtype dt, cudaStream_t s) override {
+    switch (dt) {
+      case TTALS_F64: return recon_t<double>((double*)out, s);
+      case TTALS_F32: return recon_t<float>((float*)out, s);
+      case TTALS_F16: return recon_t<__half>((__half*)out, s);
+      case TTALS_BF16: return recon_t<__nv_bfloat16>((__nv_bfloat16*)out, s);
+    }
+    return TTALS_EINVAL;
+  }
+  template <typename TO>
+  ttals_status recon_t(TO* out, cudaStream_t s) {
+    if (kstar == 1) {
+      const int nb = (int)std::min<long long>(cdiv(rest[0], 256), 4 * kSMs);
+      k_convert<TC, TO><<<nb, 256, 0, s>>>(C[par], out, rest[0]);
+      TT_CUDA(cudaGetLastError());
+      return TTALS_OK;
+    }
+    const TC* T = C[par];
+    for (int k = kstar - 1; k >= 1; --k) {
+      GemmShape g = plan_gemm(rows(k), (int)rest[k], rk(k), false);
+      if (k == 1) {
+        TT_TRY((gemm<TC, TC, TC, TO, true, false>(g, G[par][0], rk(1), T, rest[1], out, rest[1], 1, 0, nullptr,
+                                                  nullptr, nullptr, nullptr, s)));
+      } else {
+        TC* dst = Bhat[k - 1];
+        TT_TRY((gemm<TC, TC, TC, TC, true, false>(g, G[par][k - 1], rk(k), T, rest[k], dst, rest[k], 1, 0, nullptr,
+                                                  nullptr, nullptr, nullptr, s)));
+        T = dst;
+      }
+    }
+    return TTALS_OK;
+  }
+
+  // ---- initial state / resume ---------------------------------------------------
+  ttals_status set_cores(const double* const* cores, const double* g, long long t) override {
+    cudaStream_t s = have_last ? last : (cudaStream_t)0;
+    TT_CUDA(cudaStreamSynchronize(s));
+    std::vector<double*> dc(m + 1);
+    size_t off = 0;
+    for (int k = 1; k <= m; ++k) {
+      dc[k] = dcores + off;
+      TT_CUDA(cudaMemcpy(dc[k], cores[k - 1], (size_t)core_elems(k) * 8, cudaMemcpyHostToDevice));
+      off += (size_t)core_elems(k);
+    }
+    double* dg = dcores + off;
+    TT_CUDA(cudaMemcpy(dg, g, (size_t)full[m] * 8, cudaMemcpyHostToDevice));
+    // C = G_{k*} x ... x G_m x g_n, FP64 chain from the right
+    const double* T = dg;
+    int pp = 0;
+    for (int k = m; k >= kstar; --k) {
+      GemmShape gg = plan_gemm(rows(k), (int)rest[k], rk(k), false);
+      double* dst = dtmp[pp];
+      TT_TRY((gemm<double, double, double, double, true, false>(gg, dc[k], rk(k), T, rest[k], dst, rest[k], 1, 0,
+                                                                nullptr, nullptr, nullptr, nullptr, s)));
+      T = dst;
+      pp ^= 1;
+    }
+    const long long csz = full[kstar - 1] * rest[kstar - 1];
+    const int nb = (int)std::min<long long>(cdiv(csz, 256), 4 * kSMs);
+    k_convert<double, TC><<<nb, 256, 0, s>>>(T, C[par], csz);
+    TT_CUDA(cudaGetLastError());
+    for (int k = 1; k < kstar; ++k) {
+      const int nb2 = (int)std::min<long long>(cdiv(core_elems(k), 256), 4 * kSMs);
+      k_convert<double, TC><<<nb2, 256, 0, s>>>(dc[k], G[par][k - 1], core_elems(k));
+      TT_CUDA(cudaGetLastError());
+    }
+    Ctl h{};
+    h.t = t;
+    TT_CUDA(cudaMemcpy(ctl, &h, sizeof(Ctl), cudaMemcpyHostToDevice));
+    k_norm2_to_cc<TC><<<1, 1024, 0, s>>>(C[par], csz, ctl);
+    TT_CUDA(cudaGetLastError());
+    TT_CUDA(cudaStreamSynchronize(s));
+    materialised = false;
+    return TTALS_OK;
+  }
+
+  // ---- readout --------------------------------------------------------------------
+  ttals_status materialise(cudaStream_t s) {
+    // left-orthogonal TT of C with completion: for k = k*..m, Householder QR of the
+    // (r_{k-1} I_k) x rest_k unfolding, completed to r_k columns; then E_{k+1} = Q^T E_k.
+    const long long csz = full[kstar - 1] * rest[kstar - 1];
+    const int nb = (int)std::min<long long>(cdiv(csz, 256), 4 * kSMs);
+    k_convert<TC, double><<<nb, 256, 0, s>>>(C[par], dtmp[0], csz);
+    TT_CUDA(cudaGetLastError());
+    double* Ek = dtmp[0];
+    int pp = 1;
+    for (int k = kstar; k <= m; ++k) {
+      const long long nr = rows(k);
+      const int p = (int)rest[k];
+      const int ro = rk(k);
+      k_householder<double, double><<<1, HH_THREADS, 0, s>>>(Ek, nr, p, ro, hh, mat_q[k], ro);
+      TT_CUDA(cudaGetLastError());
+      // E_{k+1}[a][j] = sum_i Q[i][a] E_k[i][j]   (ro x p)
+      double* dst = (k == m) ? mat_g : dtmp[pp];
+      GemmShape gg = plan_gemm(ro, p, nr, false);
+      TT_TRY((gemm<double, double, double, double, false, false>(gg, mat_q[k], ro, Ek, p, dst, p, 1, 0, nullptr,
+                                                                 nullptr, nullptr, nullptr, s)));
+      Ek = dst;
+      pp ^= 1;
+    }
+    materialised = true;
+    return TTALS_OK;
+  }
+
+  ttals_status get_core(int k, double* host, size_t n) override {
+    cudaStream_t s = have_last ? last : (cudaStream_t)0;
+    if (k >= kstar && !materialised) TT_TRY(materialise(s));
+    if (k < kstar) {
+      const long long ne = core_elems(k);
+      const int nb = (int)std::min<long long>(cdiv(ne, 256), 4 * kSMs);
+      k_convert<TC, double><<<nb, 256, 0, s>>>(G[par][k - 1], dout, ne);
+      TT_CUDA(cudaGetLastError());
+      TT_CUDA(cudaMemcpyAsync(host, dout, n * 8, cudaMemcpyDeviceToHost, s));
+    } else if (k <= m) {
+      TT_CUDA(cudaMemcpyAsync(host, mat_q[k], n * 8, cudaMemcpyDeviceToHost, s));
+    } else {
+      TT_CUDA(cudaMemcpyAsync(host, mat_g, n * 8, cudaMemcpyDeviceToHost, s));
+    }
+    TT_CUDA(cudaStreamSynchronize(s));
+    return TTALS_OK;
+  }
+};
+
+ttals_stream* make_impl(ttals_dtype ingest) {
+  switch (ingest) {
+    case TTALS_F64: return new Impl<double, double>();
+    case TTALS_F32: return new Impl<float, float>();
+    case TTALS_F16: return new Impl<__half, float>();
+    case TTALS_BF16: return new Impl<__nv_bfloat16, float>();
+  }
+  return nullptr;
+}
+
+ttals_status set_device(int dev) {
+  int cur = -1;
+  TT_CUDA(cudaGetDevice(&cur));
+  if (cur != dev) TT_CUDA(cudaSetDevice(dev));
+  return TTALS_OK;
+}
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+extern "C" {
+
+const char* ttals_status_string(ttals_status st) {
+  switch (st) {
+    case TTALS_OK: return "ok";
+    case TTALS_EINVAL: return "invalid argument";
+    case TTALS_ENOMEM: return "out of device memory";
+    case TTALS_ECUDA: return "CUDA error";
+    case TTALS_ENONFINITE: return "non-finite slice (not committed)";
+    case TTALS_ETIMEOUT: return "device wait timed out";
+    case TTALS_ESTATE: return "invalid state";
+  }
+  return "unknown status";
+}
+
+const char* ttals_last_error(void) { return g_last_err.c_str(); }
+
+ttals_status ttals_create(int n_slice_modes, const int64_t* dims, const int64_t* ranks, const ttals_config* cfg,
+                          ttals_stream** out) {
+  if (!out) return TTALS_EINVAL;
+  *out = nullptr;
+  if (n_slice_modes < 2 || n_slice_modes > kMaxLevels || !dims || !ranks) return TTALS_EINVAL;
+  ttals_config c{};
+  c.ingest = TTALS_F64;
+  c.seed = 0x5eedull;
+  c.device = 0;
+  if (cfg) {
+    c = *cfg;
+    for (int i = 0; i < 4; ++i)
+      if (c.reserved[i] != 0) return TTALS_EINVAL;
+    if (c.seed == 0) c.seed = 0x5eedull;
+  }
+  if (c.ingest < TTALS_F64 || c.ingest > TTALS_BF16) return TTALS_EINVAL;
+  if (c.qr_passes < 0 || c.qr_passes > 2) return TTALS_EINVAL;
+  const int m = n_slice_modes;
+  std::vector<long long> d(m), r(m);
+  long long total = 1;
+  for (int i = 0; i < m; ++i) {
+    if (dims[i] < 1 || ranks[i] < 1) return TTALS_EINVAL;
+    d[i] = dims[i];
+    r[i] = ranks[i];
+    if (total > (1ll << 40) / d[i]) return TTALS_EINVAL;
+    total *= d[i];
+  }
+  // feasible ranks: r_k <= r_{k-1} I_k and r_k <= I_{k+1} r_{k+1}, to a fixed point
+  for (;;) {
+    std::vector<long long> old = r;
+    long long prev = 1;
+    for (int k = 0; k < m; ++k) {
+      r[k] = std::min(r[k], prev * d[k]);
+      prev = r[k];
+    }
+    for (int k = m - 2; k >= 0; --k) r[k] = std::min(r[k], d[k + 1] * r[k + 1]);
+    if (r == old) break;
+  }
+  for (int k = 0; k < m; ++k)
+    if (r[k] > kMaxRank) return TTALS_EINVAL;
+  if (set_device(c.device) != TTALS_OK) return TTALS_ECUDA;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || c.device >= ndev) {
+    cudaGetLastError();
+    g_last_err = "no CUDA device";
+    return TTALS_ECUDA;
+  }
+  ttals_stream* s = make_impl(c.ingest);
+  s->m = m;
+  s->dims = d;
+  s->full.assign(m + 1, 1);
+  for (int k = 0; k < m; ++k) s->full[k + 1] = r[k];
+  s->rest.assign(m + 1, 1);
+  for (int k = m - 1; k >= 0; --k) s->rest[k] = s->rest[k + 1] * d[k];
+  s->kstar = m;
+  for (int k = 1; k <= m; ++k)
+    if (s->full[k] >= s->rest[k]) { s->kstar = k; break; }
+  s->ingest = c.ingest;
+  s->device = c.device;
+  s->qr_passes = c.qr_passes ? c.qr_passes : 2;
+  if (cudaEventCreateWithFlags(&s->ev, cudaEventDisableTiming) != cudaSuccess) {
+    delete s;
+    return TTALS_ECUDA;
+  }
+  ttals_status st = s->allocate();
+  if (st != TTALS_OK) {
+    delete s;
+    return st;
+  }
+  // default initial cores: Gaussian (SplitMix64 + Box-Muller)
+  SplitMix64 rng{c.seed};
+  std::vector<std::vector<double>> cores(m);
+  std::vector<const double*> ptrs(m);
+  for (int k = 1; k <= m; ++k) {
+    cores[k - 1].resize((size_t)s->core_elems(k));
+    for (double& v : cores[k - 1]) v = rng.gauss();
+    ptrs[k - 1] = cores[k - 1].data();
+  }
+  std::vector<double> g((size_t)s->full[m]);
+  for (double& v : g) v = rng.gauss();
+  st = s->set_cores(ptrs.data(), g.data(), 0);
+  if (st != TTALS_OK) {
+    delete s;
+    return st;
+  }
+  *out = s;
+  return TTALS_OK;
+}
+
+void ttals_destroy(ttals_stream* s) {
+  if (!s) return;
+  set_device(s->device);
+  delete s;
+}
+
+ttals_status ttals_effective_ranks(const ttals_stream* s, int64_t* ranks_out) {
+  if (!s || !ranks_out) return TTALS_EINVAL;
+  for (int k = 0; k < s->m; ++k) ranks_out[k] = s->full[k + 1];
+  return TTALS_OK;
+}
+
+ttals_status ttals_set_cores(ttals_stream* s, const double* const* cores, const double* g, int64_t t) {
+  if (!s || !cores || !g || t < 0) return TTALS_EINVAL;
+  for (int k = 0; k < s->m; ++k)
+    if (!cores[k]) return TTALS_EINVAL;
+  TT_TRY(set_device(s->device));
+  return s->set_cores(cores, g, t);
+}
+
+ttals_status ttals_push_slice(ttals_stream* s, const void* slice_dev, ttals_dtype dtype, void* cuda_stream) {
+  if (!s || !slice_dev) return TTALS_EINVAL;
+  if (dtype != s->ingest) return TTALS_EINVAL;
+  if (((uintptr_t)slice_dev & 15u) != 0) return TTALS_EINVAL;
+  TT_TRY(set_device(s->device));
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  TT_TRY(s->order_after_last(st));
+  return s->push(slice_dev, st);
+}
+
+ttals_status ttals_reconstruct(ttals_stream* s, void* out_dev, ttals_dtype out_dtype, void* cuda_stream) {
+  if (!s || !out_dev) return TTALS_EINVAL;
+  if (out_dtype < TTALS_F64 || out_dtype > TTALS_BF16) return TTALS_EINVAL;
+  if (((uintptr_t)out_dev & (dtype_size(out_dtype) - 1)) != 0) return TTALS_EINVAL;
+  TT_TRY(set_device(s->device));
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  TT_TRY(s->order_after_last(st));
+  return s->reconstruct(out_dev, out_dtype, st);
+}
+
+ttals_status ttals_cores(ttals_stream* s, int k, double* host_out, size_t n_elems) {
+  if (!s || !host_out || k < 1 || k > s->m + 1) return TTALS_EINVAL;
+  const size_t want = (k <= s->m) ? (size_t)s->core_elems(k) : (size_t)s->full[s->m];
+  if (n_elems != want) return TTALS_EINVAL;
+  TT_TRY(set_device(s->device));
+  TT_TRY(s->get_core(k, host_out, n_elems));
+  Ctl h;
+  TT_TRY(s->sync_and_read(&h, true));
+  return h.latched ? (ttals_status)h.latched : TTALS_OK;
+}
+
+ttals_status ttals_stats(ttals_stream* s, double out[4]) {
+  if (!s || !out) return TTALS_EINVAL;
+  TT_TRY(set_device(s->device));
+  Ctl h;
+  TT_TRY(s->sync_and_read(&h, true));
+  out[0] = h.xx;
+  out[1] = h.ee;
+  out[2] = h.sum_xx;
+  out[3] = h.sum_ee;
+  return h.latched ? (ttals_status)h.latched : TTALS_OK;
+}
+
+ttals_status ttals_step(ttals_stream* s, int64_t* t_out) {
+  if (!s || !t_out) return TTALS_EINVAL;
+  TT_TRY(set_device(s->device));
+  Ctl h;
+  TT_TRY(s->sync_and_read(&h, true));
+  *t_out = h.t;
+  return h.latched ? (ttals_status)h.latched : TTALS_OK;
+}
+
+ttals_status ttals_sync(ttals_stream* s) {
+  if (!s) return TTALS_EINVAL;
+  TT_TRY(set_device(s->device));
+  Ctl h;
+  TT_TRY(s->sync_and_read(&h, true));
+  return h.latched ? (ttals_status)h.latched : TTALS_OK;
+}
+
+size_t ttals_device_bytes(const ttals_stream* s) { return s ? s->bytes : 0; }
+
+uint64_t ttals_launch_count(const ttals_stream* s) { return s ? (uint64_t)s->nlaunch : 0; }
+
+ttals_status ttals_stats_async(ttals_stream* s, double* out4, void* cuda_stream) {
+  if (!s || !out4) return TTALS_EINVAL;
+  TT_TRY(set_device(s->device));
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  TT_TRY(s->order_after_last(st));
+  TT_CUDA(cudaMemcpyAsync(out4, &s->ctl->xx, 4 * sizeof(double), cudaMemcpyDefault, st));
+  return TTALS_OK;
+}
+
+ttals_status ttals_profile(ttals_stream* s, int enable) {
+  if (!s) return TTALS_EINVAL;
+  TT_TRY(set_device(s->device));
+  if (s->have_last) TT_CUDA(cudaStreamSynchronize(s->last));
+  s->profiling = enable != 0;
+  s->ev_used = 0;
+  return TTALS_OK;
+}
+
+ttals_status ttals_profile_read(ttals_stream* s, double ms_out[3], int64_t* n_out) {
+  if (!s || !ms_out || !n_out) return TTALS_EINVAL;
+  TT_TRY(set_device(s->device));
+  if (s->have_last) TT_CUDA(cudaStreamSynchronize(s->last));
+  double acc[3] = {0.0, 0.0, 0.0};
+  const size_t npush = s->ev_used / ttals_stream::kProfEvents;
+  for (size_t i = 0; i < npush; ++i) {
+    cudaEvent_t* e = &s->ev_pool[i * ttals_stream::kProfEvents];
+    float a = 0.f, b = 0.f, c = 0.f;
+    if (s->kstar > 1) {
+      TT_CUDA(cudaEventElapsedTime(&a, e[1], e[2]));
+      TT_CUDA(cudaEventElapsedTime(&b, e[3], e[4]));
+    }
+    TT_CUDA(cudaEventElapsedTime(&c, e[0], e[5]));
+    acc[0] += a;
+    acc[1] += b;
+    acc[2] += c;
+  }
+  for (int i = 0; i < 3; ++i) ms_out[i] = acc[i];
+  *n_out = (int64_t)npush;
+  s->ev_used = 0;
+  return TTALS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,211 @@
+"""Thin Python binding of the libttals C ABI (include/ttals.h).
+
+Argument marshalling only: every step of the update runs in the library's CUDA
+kernels.  PyTorch supplies device memory and CUDA streams.  There is no CPU
+fallback: if the library or a CUDA device is missing, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libttals.so")
+
+F64, F32, F16, BF16 = 0, 1, 2, 3
+DTYPES = {"f64": F64, "f32": F32, "f16": F16, "bf16": BF16}
+STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENONFINITE", 5: "ETIMEOUT", 6: "ESTATE"}
+
+# every symbol include/ttals.h declares (checked by the ABI test)
+EXPORTS = ("ttals_create", "ttals_destroy", "ttals_effective_ranks", "ttals_set_cores",
+           "ttals_push_slice", "ttals_reconstruct", "ttals_cores", "ttals_stats", "ttals_step",
+           "ttals_sync", "ttals_device_bytes", "ttals_status_string", "ttals_last_error",
+           "ttals_launch_count", "ttals_stats_async", "ttals_profile", "ttals_profile_read")
+
+
+class TTALSError(RuntimeError):
+    def __init__(self, code: int, where: str, msg: str = ""):
+        self.code = code
+        self.name = STATUS.get(code, str(code))
+        super().__init__(f"{where}: {self.name}" + (f" ({msg})" if msg else ""))
+
+
+class Config(ctypes.Structure):
+    _fields_ = [("ingest", ctypes.c_int), ("seed", ctypes.c_uint64), ("device", ctypes.c_int),
+                ("qr_passes", ctypes.c_int), ("reserved", ctypes.c_int * 4)]
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load libttals.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise FileNotFoundError(f"{path} is missing; build it with python -m paper_2606_31061_b300.build")
+    lib = ctypes.CDLL(path)
+    P, I64P, VP = ctypes.POINTER, ctypes.POINTER(ctypes.c_int64), ctypes.c_void_p
+    sig = {
+        "ttals_create": (ctypes.c_int, [ctypes.c_int, I64P, I64P, P(Config), P(VP)]),
+        "ttals_destroy": (None, [VP]),
+        "ttals_effective_ranks": (ctypes.c_int, [VP, I64P]),
+        "ttals_set_cores": (ctypes.c_int, [VP, P(P(ctypes.c_double)), P(ctypes.c_double), ctypes.c_int64]),
+        "ttals_push_slice": (ctypes.c_int, [VP, VP, ctypes.c_int, VP]),
+        "ttals_reconstruct": (ctypes.c_int, [VP, VP, ctypes.c_int, VP]),
+        "ttals_cores": (ctypes.c_int, [VP, ctypes.c_int, P(ctypes.c_double), ctypes.c_size_t]),
+        "ttals_stats": (ctypes.c_int, [VP, P(ctypes.c_double)]),
+        "ttals_step": (ctypes.c_int, [VP, I64P]),
+        "ttals_sync": (ctypes.c_int, [VP]),
+        "ttals_device_bytes": (ctypes.c_size_t, [VP]),
+        "ttals_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+        "ttals_last_error": (ctypes.c_char_p, []),
+        "ttals_launch_count": (ctypes.c_uint64, [VP]),
+        "ttals_stats_async": (ctypes.c_int, [VP, VP, VP]),
+        "ttals_profile": (ctypes.c_int, [VP, ctypes.c_int]),
+        "ttals_profile_read": (ctypes.c_int, [VP, P(ctypes.c_double), I64P]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(code: int, where: str):
+    if code != 0:
+        msg = load().ttals_last_error().decode() if code == 3 else ""
+        raise TTALSError(code, where, msg)
+
+
+def _i64(seq):
+    return (ctypes.c_int64 * len(seq))(*[int(v) for v in seq])
+
+
+def _stream_handle(stream) -> Optional[int]:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+class Stream:
+    """One Online TT-ALS stream (a ttals_stream handle)."""
+
+    def __init__(self, dims: Sequence[int], ranks: Sequence[int], ingest: str = "f64",
+                 seed: int = 0x5EED, device: int = 0, qr_passes: int = 0):
+        lib = load()
+        self.dims = tuple(int(d) for d in dims)
+        self.ingest = ingest
+        cfg = Config(DTYPES[ingest], seed, device, qr_passes, (ctypes.c_int * 4)(0, 0, 0, 0))
+        h = ctypes.c_void_p()
+        _check(lib.ttals_create(len(self.dims), _i64(self.dims), _i64(ranks), ctypes.byref(cfg),
+                                ctypes.byref(h)), "ttals_create")
+        self._h = h
+        out = (ctypes.c_int64 * len(self.dims))()
+        _check(lib.ttals_effective_ranks(h, out), "ttals_effective_ranks")
+        self.ranks = tuple(int(v) for v in out)
+        self.full = (1,) + self.ranks
+
+    # -- lifetime
+    def close(self):
+        if getattr(self, "_h", None):
+            load().ttals_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # -- calls
+    def set_cores(self, cores, g, t: int = 0):
+        arrs = [np.ascontiguousarray(c, dtype=np.float64) for c in cores]
+        for k, a in enumerate(arrs):
+            want = (self.full[k], self.dims[k], self.full[k + 1])
+            if a.shape != want:
+                raise ValueError(f"core {k + 1} shape {a.shape} != {want}")
+        gg = np.ascontiguousarray(g, dtype=np.float64).reshape(-1)
+        ptrs = (ctypes.POINTER(ctypes.c_double) * len(arrs))(
+            *[a.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) for a in arrs])
+        _check(load().ttals_set_cores(self._h, ptrs, gg.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                      int(t)), "ttals_set_cores")
+
+    def push(self, slice_tensor, stream=None):
+        """Enqueue one update for a contiguous device tensor of the ingest dtype."""
+        _check(load().ttals_push_slice(self._h, ctypes.c_void_p(slice_tensor.data_ptr()),
+                                       DTYPES[self.ingest], ctypes.c_void_p(_stream_handle(stream))),
+               "ttals_push_slice")
+
+    def push_ptr(self, ptr: int, stream_handle: int):
+        _check(load().ttals_push_slice(self._h, ctypes.c_void_p(ptr), DTYPES[self.ingest],
+                                       ctypes.c_void_p(stream_handle)), "ttals_push_slice")
+
+    def reconstruct(self, out_tensor, dtype: str = "f64", stream=None):
+        _check(load().ttals_reconstruct(self._h, ctypes.c_void_p(out_tensor.data_ptr()), DTYPES[dtype],
+                                        ctypes.c_void_p(_stream_handle(stream))), "ttals_reconstruct")
+
+    def core(self, k: int) -> np.ndarray:
+        m = len(self.dims)
+        shape = (self.full[k - 1], self.dims[k - 1], self.full[k]) if k <= m else (self.full[m],)
+        out = np.empty(shape, dtype=np.float64)
+        _check(load().ttals_cores(self._h, k, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                  out.size), "ttals_cores")
+        return out
+
+    def cores(self):
+        m = len(self.dims)
+        return [self.core(k) for k in range(1, m + 1)], self.core(m + 1)
+
+    def stats(self) -> np.ndarray:
+        out = (ctypes.c_double * 4)()
+        _check(load().ttals_stats(self._h, out), "ttals_stats")
+        return np.array(list(out))
+
+    def step(self) -> int:
+        t = ctypes.c_int64()
+        _check(load().ttals_step(self._h, ctypes.byref(t)), "ttals_step")
+        return t.value
+
+    def sync(self):
+        _check(load().ttals_sync(self._h), "ttals_sync")
+
+    def sync_status(self) -> int:
+        """ttals_sync's status code without raising."""
+        return load().ttals_sync(self._h)
+
+    @property
+    def device_bytes(self) -> int:
+        return int(load().ttals_device_bytes(self._h))
+
+    @property
+    def launch_count(self) -> int:
+        return int(load().ttals_launch_count(self._h))
+
+    def stats_async(self, out_ptr: int, stream=None):
+        _check(load().ttals_stats_async(self._h, ctypes.c_void_p(out_ptr),
+                                        ctypes.c_void_p(_stream_handle(stream))), "ttals_stats_async")
+
+    def profile(self, enable: bool):
+        _check(load().ttals_profile(self._h, 1 if enable else 0), "ttals_profile")
+
+    def profile_read(self):
+        """(ms level-1 solve, ms level-1 environment, ms whole update, pushes) since the last read."""
+        ms = (ctypes.c_double * 3)()
+        n = ctypes.c_int64()
+        _check(load().ttals_profile_read(self._h, ms, ctypes.byref(n)), "ttals_profile_read")
+        return ms[0], ms[1], ms[2], n.value

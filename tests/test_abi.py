@@ -1,0 +1,68 @@
+"""The C-ABI library loads and exports every symbol include/ttals.h declares (no GPU needed)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2606_31061_b300 import ttals as T
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "ttals.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(ttals_[a-z_0-9]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2606_31061_b300 import build
+    build.build()
+    return T.load()
+
+
+def test_every_declared_symbol_is_exported(lib):
+    decl = _declared()
+    assert decl, "no declarations parsed"
+    assert sorted(T.EXPORTS) == decl
+    for name in decl:
+        assert hasattr(lib, name), name
+
+
+def test_status_strings(lib):
+    for code, name in T.STATUS.items():
+        assert lib.ttals_status_string(code)
+    assert lib.ttals_status_string(99) == b"unknown status"
+
+
+def test_invalid_arguments_rejected_before_cuda(lib):
+    h = ctypes.c_void_p()
+    dims = (ctypes.c_int64 * 2)(4, 0)
+    ranks = (ctypes.c_int64 * 2)(2, 2)
+    assert lib.ttals_create(2, dims, ranks, None, ctypes.byref(h)) == 1      # EINVAL: I_2 = 0
+    dims = (ctypes.c_int64 * 1)(4)
+    assert lib.ttals_create(1, dims, ranks, None, ctypes.byref(h)) == 1      # one slice mode
+    cfg = T.Config(7, 1, 0, 0, (ctypes.c_int * 4)(0, 0, 0, 0))
+    dims = (ctypes.c_int64 * 2)(4, 4)
+    assert lib.ttals_create(2, dims, ranks, ctypes.byref(cfg), ctypes.byref(h)) == 1   # bad dtype
+    cfg = T.Config(0, 1, 0, 0, (ctypes.c_int * 4)(1, 0, 0, 0))
+    assert lib.ttals_create(2, dims, ranks, ctypes.byref(cfg), ctypes.byref(h)) == 1   # reserved != 0
+    ranks = (ctypes.c_int64 * 2)(65, 65)
+    dims = (ctypes.c_int64 * 2)(100, 100)
+    assert lib.ttals_create(2, dims, ranks, None, ctypes.byref(h)) == 1      # rank above 64
+    assert lib.ttals_push_slice(None, None, 0, None) == 1
+    assert lib.ttals_sync(None) == 1
+    assert lib.ttals_device_bytes(None) == 0
+
+
+def test_no_device_fails_loudly(lib):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a CUDA device is present")
+    h = ctypes.c_void_p()
+    dims = (ctypes.c_int64 * 2)(8, 8)
+    ranks = (ctypes.c_int64 * 2)(2, 2)
+    assert lib.ttals_create(2, dims, ranks, None, ctypes.byref(h)) == 3      # ECUDA, no fallback
+    assert not h.value
