@@ -18,7 +18,10 @@
 //   Y = X_(1) C^T,  G_1 = orth(Y),  C = G_1^T X_(1).
 #include "ttals.h"
 #include "ttals_kernels.cuh"
+#include "ttals_fast.cuh"
 
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -95,6 +98,34 @@ struct SplitMix64 {
     return std::sqrt(-2.0 * std::log(u1)) * std::cos(6.283185307179586 * u2);
   }
 };
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no libcuda link)
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+  }
+  return fn;
+}
+
+// 2-D map of a row-major rows x cols matrix of 16-bit elements, box (64 cols) x box_rows,
+// 128-byte swizzle, out-of-range elements read as zero
+bool encode_map_2d(CUtensorMap* map, const void* base, bool bf16, long long rows, long long cols, int box_rows) {
+  PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+  if (!enc) return false;
+  cuuint64_t dim[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  cuuint64_t stride[1] = {(cuuint64_t)cols * 2};
+  cuuint32_t box[2] = {64u, (cuuint32_t)box_rows};
+  cuuint32_t estr[2] = {1u, 1u};
+  CUresult r = enc(map, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2,
+                   const_cast<void*>(base), dim, stride, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                   CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
 
 size_t dtype_size(ttals_dtype d) {
   switch (d) {
@@ -227,6 +258,29 @@ struct Impl final : ttals_stream {
   bool materialised = false;
   size_t part_elems = 0, y_elems = 0, wpart_elems = 0, sumsq_elems = 0, cc_elems = 0, hh_elems = 0;
 
+  // ---- fused tensor-core path (k* = 2, FP16 / BF16 ingest) -------------------
+  static constexpr bool kHalfIngest = std::is_same<TX, __half>::value || std::is_same<TX, __nv_bfloat16>::value;
+  bool fast = false;
+  int np_ = 16;                 // rank padded to a multiple of 16
+  int k1_rows = 0, k1_split = 1, k2_cols = 0, k2_nq = 1, k2_rch = 16;
+  long long k1_kchunk = 64;
+  size_t k1_smem = 0, k2_smem = 0;
+  float* fQ[2] = {};            // Q1 (I_1 x r)
+  float* fC[2] = {};            // F = Q1^T X (r x rest_1): right part of the state
+  TX* fCh[2] = {};              // ingest-type copy of F (scaled by 2^-shift)
+  float* fW2[2] = {};           // Q1^T Q1
+  int* fShift = nullptr;        // [2]
+  bool finalized[2] = {true, true};
+  float* fY = nullptr;
+  float* fGram = nullptr;
+  double* fXX = nullptr;
+  TX* fQh = nullptr;            // Q1 in the ingest type, I_1 x NP (operand of the env kernel)
+  float* fNx = nullptr;         // W2^{-1} - I (r x r)
+  float* fQfb = nullptr;
+  double* fCC = nullptr;
+  unsigned* fCounter = nullptr; // [2]
+  CUtensorMap mapB[2];          // TMA maps of fCh[p] (r x rest_1, box 64 x NP)
+
   int rows(int k) const { return (int)(full[k - 1] * dims[k - 1]); }  // r_{k-1} I_k
   int rk(int k) const { return (int)full[k]; }
 
@@ -284,6 +338,254 @@ struct Impl final : ttals_stream {
     TT_TRY(dalloc(&ctl, 1));
     TT_CUDA(cudaMemset(ctl, 0, sizeof(Ctl)));
     TT_CUDA(cudaFuncSetAttribute(k_factor, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024));
+    TT_CUDA(cudaFuncSetAttribute(fast::k_chol64_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024));
+    TT_TRY(setup_fast());
+    return TTALS_OK;
+  }
+
+  template <int NP>
+  ttals_status set_fast_attrs() {
+    if constexpr (kHalfIngest) {
+      TT_CUDA(cudaFuncSetAttribute(fast::k_fast_solve<TX, NP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)k1_smem));
+      TT_CUDA(cudaFuncSetAttribute(fast::k_fast_env<TX, NP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)k2_smem));
+      TT_CUDA(cudaFuncSetAttribute(fast::k_fast_factor<TX, NP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)fast::k1b_smem_bytes((int)dims[0], rk(1), NP)));
+    }
+    return TTALS_OK;
+  }
+
+  // the fused path covers k* = 2 with FP16/BF16 ingest, r_1 <= 64, rows of the slice
+  // 16-byte aligned (rest_1 % 8 == 0) and I_1 small enough for one cluster of row chunks
+  ttals_status setup_fast() {
+    if (!kHalfIngest || kstar != 2) return TTALS_OK;
+    const long long M = dims[0], J = rest[1];
+    const int r = rk(1);
+    if (J % 8 != 0 || r > 64 || M > 8 * 512) return TTALS_OK;
+    np_ = ((r + 15) / 16) * 16;
+    // the factor cluster holds 1/8 of Y and Q1 per CTA in shared memory (plus ~37 KB static)
+    if (fast::k1b_smem_bytes((int)M, r, np_) + 40 * 1024 > 227 * 1024) {
+      np_ = 16;
+      return TTALS_OK;
+    }
+    k1_rows = (int)cdiv(M, fast::K1_BM);
+    k1_split = 8;
+    while (k1_split > 1 && (long long)k1_rows * k1_split > 2 * kSMs) k1_split >>= 1;
+    k1_kchunk = cdiv(cdiv(J, k1_split), fast::K1_BK) * fast::K1_BK;
+    k2_cols = (int)cdiv(J, fast::K2_BN);
+    // row chunks per cluster: the fewest (largest chunks) that keep two env CTAs per SM
+    auto k2_bytes = [&](int rch) -> size_t {
+      switch (np_) {
+        case 16: return fast::k2_smem_bytes<16>(rch, r);
+        case 32: return fast::k2_smem_bytes<32>(rch, r);
+        case 48: return fast::k2_smem_bytes<48>(rch, r);
+        default: return fast::k2_smem_bytes<64>(rch, r);
+      }
+    };
+    k2_nq = 0;
+    for (int nq = (int)std::max<long long>(1, std::min<long long>(8, cdiv(M, 256))); nq <= 8; ++nq) {
+      const int rch = (int)(cdiv(cdiv(M, nq), 16) * 16);
+      if (k2_bytes(rch) <= 113 * 1024) {
+        k2_nq = nq;
+        break;
+      }
+    }
+    if (k2_nq == 0) k2_nq = 8;
+    k2_rch = (int)(cdiv(cdiv(M, k2_nq), 16) * 16);
+    k2_smem = k2_bytes(k2_rch);
+    switch (np_) {
+      case 16: k1_smem = fast::k1_smem_bytes<16>(); break;
+      case 32: k1_smem = fast::k1_smem_bytes<32>(); break;
+      case 48: k1_smem = fast::k1_smem_bytes<48>(); break;
+      default: k1_smem = fast::k1_smem_bytes<64>(); break;
+    }
+    // after the main loop the solve CTA reuses its buffers: P (64 x NP), Gram (r x r), rows
+    k1_smem = std::max(k1_smem, (size_t)(64 * np_ + r * r + 64 * r) * 4 + 64);
+    if (k2_smem > 220 * 1024 || k2_rch > 256) return TTALS_OK;
+    if (!tensor_map_encoder()) return TTALS_OK;
+    switch (np_) {
+      case 16: TT_TRY(set_fast_attrs<16>()); break;
+      case 32: TT_TRY(set_fast_attrs<32>()); break;
+      case 48: TT_TRY(set_fast_attrs<48>()); break;
+      default: TT_TRY(set_fast_attrs<64>()); break;
+    }
+    for (int p = 0; p < 2; ++p) {
+      TT_TRY(dalloc(&fQ[p], (size_t)(M * r)));
+      TT_TRY(dalloc(&fC[p], (size_t)(r * J)));
+      TT_TRY(dalloc(&fCh[p], (size_t)(r * J)));
+      TT_TRY(dalloc(&fW2[p], (size_t)(r * r)));
+    }
+    TT_TRY(dalloc(&fShift, 2));
+    TT_TRY(dalloc(&fY, (size_t)(M * r)));
+    TT_TRY(dalloc(&fGram, (size_t)k1_rows * r * r));
+    TT_TRY(dalloc(&fXX, (size_t)k1_rows));
+    TT_TRY(dalloc(&fQh, (size_t)(M * np_)));
+    TT_TRY(dalloc(&fNx, (size_t)r * r));
+    TT_TRY(dalloc(&fQfb, (size_t)(M * r)));
+    TT_TRY(dalloc(&fCC, (size_t)k2_cols));
+    TT_TRY(dalloc(&fCounter, 2));
+    TT_CUDA(cudaMemset(fCounter, 0, 2 * sizeof(unsigned)));
+    const bool bf = std::is_same<TX, __nv_bfloat16>::value;
+    for (int p = 0; p < 2; ++p)
+      if (!encode_map_2d(&mapB[p], fCh[p], bf, r, J, np_)) return TTALS_OK;
+    TT_CUDA(cudaMemset(fShift, 0, 2 * sizeof(int)));
+    hh_elems = std::max<size_t>(hh_elems, (size_t)(2 * M * r));
+    fast = true;
+    return TTALS_OK;
+  }
+
+  template <int NP>
+  ttals_status launch_fast(const TX* X, cudaStream_t s) {
+    if constexpr (kHalfIngest) {
+      const int np = 1 - par;
+      const int r = rk(1);
+      cudaLaunchAttribute at[2];
+      at[0].id = cudaLaunchAttributeClusterDimension;
+      at[0].val.clusterDim.x = 1;
+      at[0].val.clusterDim.y = (unsigned)k1_split;
+      at[0].val.clusterDim.z = 1;
+      at[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+      at[1].val.programmaticStreamSerializationAllowed = profiling ? 0 : 1;
+      // TMA maps of this slice (box 64 x 64 for the solve, 64 x rch for the env kernel)
+      const bool bf = std::is_same<TX, __nv_bfloat16>::value;
+      CUtensorMap mapX1, mapX2;
+      if (!encode_map_2d(&mapX1, X, bf, dims[0], rest[1], fast::K1_BM) ||
+          !encode_map_2d(&mapX2, X, bf, dims[0], rest[1], k2_rch)) {
+        g_last_err = "cuTensorMapEncodeTiled failed";
+        return TTALS_ECUDA;
+      }
+      // K1: local solve
+      fast::SolveArgs a1{};
+      a1.M = (int)dims[0];
+      a1.r = r;
+      a1.K = rest[1];
+      a1.kchunk = k1_kchunk;
+      a1.Y = fY;
+      a1.gram_part = fGram;
+      a1.xx_part = fXX;
+      a1.ctl = ctl;
+      cudaLaunchConfig_t c1{};
+      c1.gridDim = dim3((unsigned)k1_rows, (unsigned)k1_split, 1);
+      c1.blockDim = dim3(fast::K1_THREADS, 1, 1);
+      c1.dynamicSmemBytes = k1_smem;
+      c1.stream = s;
+      c1.attrs = at;
+      c1.numAttrs = 2;
+      TT_TRY(mark(1, s));
+      TT_CUDA(cudaLaunchKernelEx(&c1, fast::k_fast_solve<TX, NP>, mapX1, mapB[par], a1));
+      ++nlaunch;
+      // K1b: r x r factor, Q1, W2, Nx
+      fast::FactorArgs ab{};
+      ab.Y = fY;
+      ab.gram_part = fGram;
+      ab.xx_part = fXX;
+      ab.nrt = k1_rows;
+      ab.M = (int)dims[0];
+      ab.r = r;
+      ab.Qh = fQh;
+      ab.Qst = fQ[np];
+      ab.W2st = fW2[np];
+      ab.Nx = fNx;
+      ab.hh_work = hh;
+      ab.Qfb = fQfb;
+      ab.ctl = ctl;
+      cudaLaunchAttribute atb[2];
+      atb[0] = at[0];
+      atb[0].val.clusterDim.y = (unsigned)fast::KB_CLUSTER;
+      atb[1] = at[1];
+      cudaLaunchConfig_t cb{};
+      cb.gridDim = dim3(1, (unsigned)fast::KB_CLUSTER, 1);
+      cb.blockDim = dim3(fast::K1B_THREADS, 1, 1);
+      cb.dynamicSmemBytes = fast::k1b_smem_bytes((int)dims[0], r, NP);
+      cb.stream = s;
+      cb.attrs = atb;
+      cb.numAttrs = 2;
+      TT_CUDA(cudaLaunchKernelEx(&cb, fast::k_fast_factor<TX, NP>, ab));
+      ++nlaunch;
+      TT_TRY(mark(2, s));
+      // K2: environment
+      fast::EnvArgs a2{};
+      a2.M = (int)dims[0];
+      a2.r = r;
+      a2.J = rest[1];
+      a2.rch = k2_rch;
+      a2.Qh = fQh;
+      a2.Nx = fNx;
+      a2.Cst = fC[np];
+      a2.Chst = fCh[np];
+      a2.ch_shift = fShift + np;
+      a2.cc_part = fCC;
+      a2.counter = fCounter + 1;
+      a2.ctl = ctl;
+      a2.Qst = fQ[np];
+      a2.W2st = fW2[np];
+      a2.Qold = fQ[par];
+      a2.Cold = fC[par];
+      a2.Chold = fCh[par];
+      a2.W2old = fW2[par];
+      a2.ch_shift_old = fShift + par;
+      a2.is_half = std::is_same<TX, __half>::value ? 1 : 0;
+      at[0].val.clusterDim.y = (unsigned)k2_nq;
+      cudaLaunchConfig_t c2{};
+      c2.gridDim = dim3((unsigned)k2_cols, (unsigned)k2_nq, 1);
+      c2.blockDim = dim3(fast::K2_THREADS, 1, 1);
+      c2.dynamicSmemBytes = k2_smem;
+      c2.stream = s;
+      c2.attrs = at;
+      c2.numAttrs = 2;
+      TT_TRY(mark(3, s));
+      TT_CUDA(cudaLaunchKernelEx(&c2, fast::k_fast_env<TX, NP>, mapX2, a2));
+      ++nlaunch;
+      TT_TRY(mark(4, s));
+      finalized[np] = false;
+      materialised = false;
+      par = np;
+    }
+    return TTALS_OK;
+  }
+
+  ttals_status push_fast(const TX* X, cudaStream_t s) {
+    switch (np_) {
+      case 16: return launch_fast<16>(X, s);
+      case 32: return launch_fast<32>(X, s);
+      case 48: return launch_fast<48>(X, s);
+      default: return launch_fast<64>(X, s);
+    }
+  }
+
+  // fused-path state -> orthonormal-gauge cores G_1 = Q1 R2^{-1}, C = R2^{-T} F
+  // (R2 = chol(Q1^T Q1), FP64), written to the generic state buffers of this parity
+  ttals_status finalize(cudaStream_t s) {
+    if (!fast || finalized[par]) return TTALS_OK;
+    const int r = rk(1);
+    const long long M = dims[0], J = rest[1];
+    fast::k_chol64_inverse<<<1, 256, (size_t)2 * r * r * 8, s>>>(fW2[par], r, T64, T32);
+    TT_CUDA(cudaGetLastError());
+    const int nb = (int)std::min<long long>(cdiv(M * r, 256), 4 * kSMs);
+    fast::k_apply_upper<<<nb, 256, 0, s>>>(fQ[par], M, r, T32, (float*)G[par][0]);
+    TT_CUDA(cudaGetLastError());
+    // C[a][j] = sum_b T[b][a] F[b][j]
+    GemmShape g = plan_gemm(r, (int)J, r, false);
+    TT_TRY((gemm<float, float, float, float, false, false>(g, T32, r, fC[par], J, (float*)C[par], J, 1, 0, nullptr,
+                                                           nullptr, nullptr, nullptr, s)));
+    finalized[par] = true;
+    return TTALS_OK;
+  }
+
+  // after set_cores: mirror the generic state into the fused-path state
+  ttals_status sync_fast_from_generic(cudaStream_t s) {
+    if constexpr (kHalfIngest) {
+      if (!fast) return TTALS_OK;
+      const int r = rk(1);
+      const long long M = dims[0], J = rest[1];
+      TT_CUDA(cudaMemcpyAsync(fQ[par], G[par][0], (size_t)(M * r) * 4, cudaMemcpyDeviceToDevice, s));
+      TT_CUDA(cudaMemcpyAsync(fC[par], C[par], (size_t)(r * J) * 4, cudaMemcpyDeviceToDevice, s));
+      fast::k_make_half_copy<TX><<<1, 1024, 0, s>>>(fC[par], r * J, fCh[par], fShift + par,
+                                                    std::is_same<TX, __half>::value ? 1 : 0);
+      TT_CUDA(cudaGetLastError());
+      finalized[par] = true;
+    }
     return TTALS_OK;
   }
 
@@ -341,6 +643,7 @@ struct Impl final : ttals_stream {
 
   ttals_status push_body(const void* xv, cudaStream_t s) {
     const TX* X = (const TX*)xv;
+    if (fast) return push_fast(X, s);
     const int np = 1 - par;
     materialised = false;
     CopyList rl{};
@@ -442,6 +745,7 @@ struct Impl final : ttals_stream {
   }
   template <typename TO>
   ttals_status recon_t(TO* out, cudaStream_t s) {
+    TT_TRY(finalize(s));
     if (kstar == 1) {
       const int nb = (int)std::min<long long>(cdiv(rest[0], 256), 4 * kSMs);
       k_convert<TC, TO><<<nb, 256, 0, s>>>(C[par], out, rest[0]);
@@ -502,6 +806,7 @@ struct Impl final : ttals_stream {
     TT_CUDA(cudaMemcpy(ctl, &h, sizeof(Ctl), cudaMemcpyHostToDevice));
     k_norm2_to_cc<TC><<<1, 1024, 0, s>>>(C[par], csz, ctl);
     TT_CUDA(cudaGetLastError());
+    TT_TRY(sync_fast_from_generic(s));
     TT_CUDA(cudaStreamSynchronize(s));
     materialised = false;
     return TTALS_OK;
@@ -537,6 +842,7 @@ struct Impl final : ttals_stream {
 
   ttals_status get_core(int k, double* host, size_t n) override {
     cudaStream_t s = have_last ? last : (cudaStream_t)0;
+    TT_TRY(finalize(s));
     if (k >= kstar && !materialised) TT_TRY(materialise(s));
     if (k < kstar) {
       const long long ne = core_elems(k);
@@ -763,6 +1069,14 @@ ttals_status ttals_sync(ttals_stream* s) {
 }
 
 size_t ttals_device_bytes(const ttals_stream* s) { return s ? s->bytes : 0; }
+
+#ifdef TTALS_TRACE
+// phase timestamps of the last traced launches (builds with -DTTALS_TRACE only)
+int ttals_debug_trace(unsigned long long* out, int n) {
+  if (n > 128) n = 128;
+  return cudaMemcpyFromSymbol(out, ttals::g_ttals_trace, (size_t)n * 8) == cudaSuccess ? 0 : 3;
+}
+#endif
 
 uint64_t ttals_launch_count(const ttals_stream* s) { return s ? (uint64_t)s->nlaunch : 0; }
 

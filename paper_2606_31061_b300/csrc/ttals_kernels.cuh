@@ -15,6 +15,24 @@
 
 namespace ttals {
 
+// Compile-time phase tracing: with -DTTALS_TRACE, TTRACE(i) stores %globaltimer (ns)
+// from thread 0 of the calling block into g_ttals_trace[i]; otherwise it is empty.
+#ifdef TTALS_TRACE
+__device__ unsigned long long g_ttals_trace[128];
+#define TTRACE(i)                                                                  \
+  do {                                                                             \
+    if (threadIdx.x == 0) {                                                        \
+      unsigned long long t_;                                                       \
+      asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t_));                       \
+      ::ttals::g_ttals_trace[(i)] = t_;                                            \
+    }                                                                              \
+  } while (0)
+#else
+#define TTRACE(i) \
+  do {            \
+  } while (0)
+#endif
+
 // --------------------------------------------------------------------------
 // control block shared by the kernels of one stream (device memory)
 // --------------------------------------------------------------------------
@@ -88,14 +106,16 @@ __device__ __forceinline__ float warp_sum(float v) {
   return v;
 }
 // sum over the block; every thread gets the result.  `sh` holds >= 32 doubles.
+// Fixed-shape tree (warp shuffles, then one warp over the warp sums): deterministic,
+// and the FP64 dependency chain stays at ~10 adds.
 __device__ __forceinline__ double block_sum(double v, double* sh) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
   v = warp_sum(v);
   __syncthreads();
   if (lane == 0) sh[w] = v;
   __syncthreads();
-  double s = 0.0;
-  for (int i = 0; i < nw; ++i) s += sh[i];   // fixed order: deterministic
+  double s = (lane < nw) ? sh[lane] : 0.0;
+  s = warp_sum(s);
   return s;
 }
 
