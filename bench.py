@@ -196,7 +196,7 @@ def time_arm(ingest, steps, warmup, pool, dist_on, sampler_idx):
     st.profile(True)
     for t in range(nprof):
         st.push_ptr(pool[pingpong(warmup + steps + t, P)].data_ptr(), h)
-    ms_solve, ms_env, ms_push, npush = st.profile_read()
+    ms_solve, ms_factor, ms_env, ms_push, npush = st.profile_read()
     st.profile(False)
     lat = []
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
@@ -209,7 +209,8 @@ def time_arm(ingest, steps, warmup, pool, dist_on, sampler_idx):
     lat = sorted(a.elapsed_time(b) for a, b in ev)
     stats = st.stats()
     st.close()
-    return dict(ms=ms, launches=launches, ms_solve=ms_solve, ms_env=ms_env, ms_push=ms_push, npush=npush,
+    return dict(ms=ms, launches=launches, ms_solve=ms_solve, ms_factor=ms_factor, ms_env=ms_env,
+                ms_push=ms_push, npush=npush,
                 lat=lat, clocks=clocks, re=math.sqrt(stats[3] / stats[2]) if stats[2] > 0 else None)
 
 
@@ -346,15 +347,21 @@ def main():
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         sec = float(t.item())
     value = args.steps * world / sec
-    slice_bytes = int(np.prod(DIMS)) * pool.element_size()
+    es = pool.element_size()
+    slice_bytes = int(np.prod(DIMS)) * es
     r1, rest1, i1 = 32, 1920 * 3, 1080
-    alg = {"solve": slice_bytes + r1 * rest1 * 4 + i1 * r1 * 4,
-           "env": slice_bytes + i1 * r1 * 4 + r1 * rest1 * 4}
-    per = {"solve": r["ms_solve"] / max(1, r["npush"]), "env": r["ms_env"] / max(1, r["npush"])}
+    # algorithmic bytes per launch: each operand read once, each result written once
+    alg = {"solve": slice_bytes + r1 * rest1 * es + i1 * r1 * 4,          # X, C (ingest copy) -> Y
+           "factor": i1 * r1 * 4 + i1 * r1 * (es + 4),                   # Y -> Q1 (ingest copy + FP32)
+           "env": slice_bytes + i1 * r1 * es + r1 * rest1 * (4 + es)}    # X, Q1 -> C (FP32 + ingest copy)
+    npush = max(1, r["npush"])
+    per = {"solve": r["ms_solve"] / npush, "factor": r["ms_factor"] / npush, "env": r["ms_env"] / npush}
     dom = max(per, key=per.get)
     peak, peak_src = peaks()
     achieved = alg[dom] / (per[dom] * 1e-3) / 1e9
-    kname = {"solve": "level-1 local solve Y = X_(1) B^_1^T", "env": "level-1 environment E_2 = G_1^T X_(1)"}[dom]
+    kname = {"solve": "level-1 local solve Y = X_(1) B^_1^T",
+             "factor": "level-1 factorisation Q1 = orth(Y)",
+             "env": "level-1 environment E_2 = G_1^T X_(1)"}[dom]
     e2e = e2e_arm(args.ingest, args.e2e_steps, pool_np, dist_on)
     e2e_sec = e2e["seconds"]
     if dist_on:
@@ -397,7 +404,8 @@ def main():
                          "peak_source": peak_src, "unit": "GB/s", "frac": achieved / peak,
                          "traffic": traffic_record(dom),
                          "algorithmic_bytes": alg[dom], "ms_per_launch": per[dom],
-                         "step_share": per[dom] / (r["ms_push"] / max(1, r["npush"]))},
+                         "step_share": per[dom] / (r["ms_push"] / npush),
+                         "ms_per_launch_all": per},
             "e2e": {"value": args.e2e_steps * world / e2e_sec, "unit": "slices/s",
                     "h2d_bytes_per_step": e2e["h2d"], "d2h_bytes_per_step": e2e["d2h"]},
             "gpu_launches": r["launches"],

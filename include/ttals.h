@@ -154,16 +154,18 @@ size_t ttals_device_bytes(const ttals_stream *s);
  *   {||x_t||^2, ||x_t - x^_t||^2, sum ||x||^2, sum ||x - x^||^2} into out4 (host
  *   pinned or device memory, 4 doubles).  Errors: EINVAL, ECUDA.
  * ttals_profile - enable (1) or disable (0) per-push timing: CUDA events recorded on
- *   the launch stream around the whole update and around the level-1 local solve
- *   Y = X_(1) B_1^T and the level-1 environment E_2 = G_1^T X_(1).  Synchronising.
+ *   the launch stream before the level-1 local solve Y = X_(1) B_1^T, after it, before
+ *   and after the level-1 environment E_2 = G_1^T X_(1), and around the whole update.
+ *   While enabled, consecutive kernels are not overlapped.  Synchronising.
  * ttals_profile_read - wait, then write the summed milliseconds over the pushes timed
- *   since the last read: ms_out[0] level-1 solve, ms_out[1] level-1 environment,
- *   ms_out[2] whole update; *n_out = number of pushes.  Resets the totals.
+ *   since the last read: ms_out[0] level-1 solve, ms_out[1] level-1 factorisation
+ *   (orthonormal basis of the solve's span), ms_out[2] level-1 environment, ms_out[3]
+ *   whole update; *n_out = number of pushes.  Resets the totals.
  */
 uint64_t ttals_launch_count(const ttals_stream *s);
 ttals_status ttals_stats_async(ttals_stream *s, double *out4, void *cuda_stream);
 ttals_status ttals_profile(ttals_stream *s, int enable);
-ttals_status ttals_profile_read(ttals_stream *s, double ms_out[3], int64_t *n_out);
+ttals_status ttals_profile_read(ttals_stream *s, double ms_out[4], int64_t *n_out);
 
 /* Static text for a status code. */
 const char *ttals_status_string(ttals_status st);

@@ -162,7 +162,7 @@ struct ttals_stream {
   bool profiling = false;
   std::vector<cudaEvent_t> ev_pool;    // recorded events, in groups of kProfEvents per push
   size_t ev_used = 0;
-  static constexpr int kProfEvents = 6; // push begin, solve1 begin/end, env1 begin/end, push end
+  static constexpr int kProfEvents = 6; // push begin, solve1 begin, solve1 end, env1 begin, env1 end, push end
 
   virtual ~ttals_stream() {
     if (have_last) cudaStreamSynchronize(last);
@@ -272,12 +272,11 @@ struct Impl final : ttals_stream {
   int* fShift = nullptr;        // [2]
   bool finalized[2] = {true, true};
   float* fY = nullptr;
-  float* fGram = nullptr;
-  double* fXX = nullptr;
+  float2* fXX = nullptr;       // float-float partials of ||x||^2 (solve CTAs)
   TX* fQh = nullptr;            // Q1 in the ingest type, I_1 x NP (operand of the env kernel)
   float* fNx = nullptr;         // W2^{-1} - I (r x r)
   float* fQfb = nullptr;
-  double* fCC = nullptr;
+  float2* fCC = nullptr;       // float-float partials of ||x^||^2 (env CTAs)
   unsigned* fCounter = nullptr; // [2]
   CUtensorMap mapB[2];          // TMA maps of fCh[p] (r x rest_1, box 64 x NP)
 
@@ -418,12 +417,11 @@ struct Impl final : ttals_stream {
     }
     TT_TRY(dalloc(&fShift, 2));
     TT_TRY(dalloc(&fY, (size_t)(M * r)));
-    TT_TRY(dalloc(&fGram, (size_t)k1_rows * r * r));
-    TT_TRY(dalloc(&fXX, (size_t)k1_rows));
+    TT_TRY(dalloc(&fXX, (size_t)k1_rows * k1_split));
     TT_TRY(dalloc(&fQh, (size_t)(M * np_)));
     TT_TRY(dalloc(&fNx, (size_t)r * r));
     TT_TRY(dalloc(&fQfb, (size_t)(M * r)));
-    TT_TRY(dalloc(&fCC, (size_t)k2_cols));
+    TT_TRY(dalloc(&fCC, (size_t)k2_cols * k2_nq));
     TT_TRY(dalloc(&fCounter, 2));
     TT_CUDA(cudaMemset(fCounter, 0, 2 * sizeof(unsigned)));
     const bool bf = std::is_same<TX, __nv_bfloat16>::value;
@@ -462,7 +460,6 @@ struct Impl final : ttals_stream {
       a1.K = rest[1];
       a1.kchunk = k1_kchunk;
       a1.Y = fY;
-      a1.gram_part = fGram;
       a1.xx_part = fXX;
       a1.ctl = ctl;
       cudaLaunchConfig_t c1{};
@@ -475,12 +472,12 @@ struct Impl final : ttals_stream {
       TT_TRY(mark(1, s));
       TT_CUDA(cudaLaunchKernelEx(&c1, fast::k_fast_solve<TX, NP>, mapX1, mapB[par], a1));
       ++nlaunch;
+      TT_TRY(mark(2, s));
       // K1b: r x r factor, Q1, W2, Nx
       fast::FactorArgs ab{};
       ab.Y = fY;
-      ab.gram_part = fGram;
       ab.xx_part = fXX;
-      ab.nrt = k1_rows;
+      ab.nxx = k1_rows * k1_split;
       ab.M = (int)dims[0];
       ab.r = r;
       ab.Qh = fQh;
@@ -503,7 +500,7 @@ struct Impl final : ttals_stream {
       cb.numAttrs = 2;
       TT_CUDA(cudaLaunchKernelEx(&cb, fast::k_fast_factor<TX, NP>, ab));
       ++nlaunch;
-      TT_TRY(mark(2, s));
+      TT_TRY(mark(3, s));
       // K2: environment
       fast::EnvArgs a2{};
       a2.M = (int)dims[0];
@@ -534,7 +531,6 @@ struct Impl final : ttals_stream {
       c2.stream = s;
       c2.attrs = at;
       c2.numAttrs = 2;
-      TT_TRY(mark(3, s));
       TT_CUDA(cudaLaunchKernelEx(&c2, fast::k_fast_env<TX, NP>, mapX2, a2));
       ++nlaunch;
       TT_TRY(mark(4, s));
@@ -1076,6 +1072,10 @@ int ttals_debug_trace(unsigned long long* out, int n) {
   if (n > 128) n = 128;
   return cudaMemcpyFromSymbol(out, ttals::g_ttals_trace, (size_t)n * 8) == cudaSuccess ? 0 : 3;
 }
+int ttals_debug_trace_cta(unsigned long long* out, int n) {
+  if (n > 2048) n = 2048;
+  return cudaMemcpyFromSymbol(out, ttals::g_ttals_cta, (size_t)n * 8) == cudaSuccess ? 0 : 3;
+}
 #endif
 
 uint64_t ttals_launch_count(const ttals_stream* s) { return s ? (uint64_t)s->nlaunch : 0; }
@@ -1098,25 +1098,24 @@ ttals_status ttals_profile(ttals_stream* s, int enable) {
   return TTALS_OK;
 }
 
-ttals_status ttals_profile_read(ttals_stream* s, double ms_out[3], int64_t* n_out) {
+ttals_status ttals_profile_read(ttals_stream* s, double ms_out[4], int64_t* n_out) {
   if (!s || !ms_out || !n_out) return TTALS_EINVAL;
   TT_TRY(set_device(s->device));
   if (s->have_last) TT_CUDA(cudaStreamSynchronize(s->last));
-  double acc[3] = {0.0, 0.0, 0.0};
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
   const size_t npush = s->ev_used / ttals_stream::kProfEvents;
   for (size_t i = 0; i < npush; ++i) {
     cudaEvent_t* e = &s->ev_pool[i * ttals_stream::kProfEvents];
-    float a = 0.f, b = 0.f, c = 0.f;
+    float t[4] = {0.f, 0.f, 0.f, 0.f};
     if (s->kstar > 1) {
-      TT_CUDA(cudaEventElapsedTime(&a, e[1], e[2]));
-      TT_CUDA(cudaEventElapsedTime(&b, e[3], e[4]));
+      TT_CUDA(cudaEventElapsedTime(&t[0], e[1], e[2]));
+      TT_CUDA(cudaEventElapsedTime(&t[1], e[2], e[3]));
+      TT_CUDA(cudaEventElapsedTime(&t[2], e[3], e[4]));
     }
-    TT_CUDA(cudaEventElapsedTime(&c, e[0], e[5]));
-    acc[0] += a;
-    acc[1] += b;
-    acc[2] += c;
+    TT_CUDA(cudaEventElapsedTime(&t[3], e[0], e[5]));
+    for (int q = 0; q < 4; ++q) acc[q] += t[q];
   }
-  for (int i = 0; i < 3; ++i) ms_out[i] = acc[i];
+  for (int i = 0; i < 4; ++i) ms_out[i] = acc[i];
   *n_out = (int64_t)npush;
   s->ev_used = 0;
   return TTALS_OK;

@@ -35,6 +35,9 @@ __device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, uint32
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(dst), "l"(src), "r"(src_bytes)
                : "memory");
 }
+__device__ __forceinline__ void cp_async4(uint32_t dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(dst), "l"(src) : "memory");
+}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void cp_async_wait() {
@@ -102,6 +105,13 @@ __device__ __forceinline__ uint32_t cluster_rank() {
 __device__ __forceinline__ void cluster_sync() {
   asm volatile("barrier.cluster.arrive.release.aligned;\nbarrier.cluster.wait.acquire.aligned;\n" ::: "memory");
 }
+// split form: every thread arrives, does independent work, then waits
+__device__ __forceinline__ void cluster_arrive() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n" ::: "memory");
+}
+__device__ __forceinline__ void cluster_wait() {
+  asm volatile("barrier.cluster.wait.acquire.aligned;\n" ::: "memory");
+}
 __device__ __forceinline__ uint32_t dsmem_addr(uint32_t local, uint32_t rank) {
   uint32_t r;
   asm volatile("mapa.shared::cluster.u32 %0, %1, %2;\n" : "=r"(r) : "r"(local), "r"(rank));
@@ -127,6 +137,39 @@ __device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float v) {
   const float bb = s - hi;
   lo += (hi - (s - bb)) + (v - bb);
   hi = s;
+}
+
+// float-float sums: hi + lo, added with TwoSum on the FP32 pipe (the FP64 pipe of this
+// part is narrow and its latency long; these sums need more than FP32 but not FP64 rate)
+__device__ __forceinline__ void ff_add(float& hi, float& lo, float bh, float bl) {
+  two_sum_acc(hi, lo, bh);
+  lo += bl;
+}
+// block-wide float-float sum in a fixed order; the result is valid in thread 0.
+// sh: 64 floats of shared memory.
+__device__ __forceinline__ float2 ff_block_sum(float hi, float lo, float* sh) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float bh = __shfl_down_sync(0xffffffffu, hi, o), bl = __shfl_down_sync(0xffffffffu, lo, o);
+    ff_add(hi, lo, bh, bl);
+  }
+  __syncthreads();
+  if (lane == 0) {
+    sh[2 * w] = hi;
+    sh[2 * w + 1] = lo;
+  }
+  __syncthreads();
+  if (w == 0) {
+    hi = lane < nw ? sh[2 * lane] : 0.f;
+    lo = lane < nw ? sh[2 * lane + 1] : 0.f;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const float bh = __shfl_down_sync(0xffffffffu, hi, o), bl = __shfl_down_sync(0xffffffffu, lo, o);
+      ff_add(hi, lo, bh, bl);
+    }
+  }
+  return make_float2(hi, lo);
 }
 
 // mbarrier and bulk-copy (TMA) helpers -----------------------------------------
@@ -193,6 +236,9 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map
 // byte offset of 16-byte chunk c of row `row` in a 128B-swizzled box (1024-byte aligned)
 __device__ __forceinline__ uint32_t swz(int row, int c) { return (uint32_t)(row * 128 + ((c ^ (row & 7)) << 4)); }
 
+__device__ __forceinline__ unsigned short tx_bits(__half v) { return __half_as_ushort(v); }
+__device__ __forceinline__ unsigned short tx_bits(__nv_bfloat16 v) { return __bfloat16_as_ushort(v); }
+
 // ================================================================ K1: local solve
 // Y = X_(1) B^T for one 64-row tile of X and a k-split; the splits of a row tile form a
 // thread-block cluster and reduce their partial tiles through distributed shared memory
@@ -208,8 +254,7 @@ struct SolveArgs {
   int M, r;
   long long K, kchunk;    // kchunk % 64 == 0
   float* Y;               // M x r
-  float* gram_part;       // [row tiles][r*r]
-  double* xx_part;        // [row tiles]
+  float2* xx_part;        // [row tiles * splits] float-float partials of ||x||^2
   Ctl* ctl;
 };
 
@@ -231,8 +276,7 @@ __global__ void __launch_bounds__(K1_THREADS, 2)
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
   __shared__ __align__(8) uint64_t bars[K1_STAGES];
-  __shared__ double red[32];
-  __shared__ double ss_sh;
+  __shared__ float redf[64];
   __shared__ int timeout_flag;
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -241,7 +285,7 @@ __global__ void __launch_bounds__(K1_THREADS, 2)
   const int nsplit = gridDim.y;
   const int rt = blockIdx.x;
   const int m0 = rt * K1_BM;
-  const int r = a.r, rr = r * r;
+  const int r = a.r;
   const long long kbeg = (long long)blockIdx.y * a.kchunk;
   const long long kend = (kbeg + a.kchunk < a.K) ? kbeg + a.kchunk : a.K;
   const int ntk = kend > kbeg ? (int)((kend - kbeg + K1_BK - 1) / K1_BK) : 0;
@@ -257,6 +301,7 @@ __global__ void __launch_bounds__(K1_THREADS, 2)
   }
   __syncthreads();
   if (tr0) TTRACE(0);
+  TTRACE_CTA(0);
   // A tiles do not depend on the previous kernel: start them before the dependency wait
   if (tid == 0) {
     for (int t = 0; t < K1_STAGES && t < ntk; ++t) {
@@ -292,10 +337,11 @@ __global__ void __launch_bounds__(K1_THREADS, 2)
   float acc[NT][4];
 #pragma unroll
   for (int j = 0; j < NT; ++j) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.f;
-  double ssd = 0.0;
+  float ssh = 0.f, ssl = 0.f;    // ||x||^2 of the tiles seen by this thread (float-float)
   for (int t = 0; t < ntk; ++t) {
     const int st = t % K1_STAGES;
     if (!mbar_wait(smem_u32(&bars[st]), (uint32_t)((t / K1_STAGES) & 1))) timeout_flag = 1;
+    if (t == 0) TTRACE_CTA(1);
     const uint32_t tA = stageA(st), tB = stageB(st);
     float ss = 0.f;
 #pragma unroll
@@ -321,7 +367,7 @@ __global__ void __launch_bounds__(K1_THREADS, 2)
         mma16816<TX>(acc[NT - 1], af, b0, b1);
       }
     }
-    ssd += (double)ss;
+    two_sum_acc(ssh, ssl, ss);
     __syncthreads();          // every warp is done with stage st
     if (t == 0 && bzero && blockIdx.y == 0 && tid == 0)
       *reinterpret_cast<TX*>(smem + (stageB(0) - sbase)) = from_acc<TX>(0.f);
@@ -339,6 +385,7 @@ __global__ void __launch_bounds__(K1_THREADS, 2)
     }
   }
   if (tr0) TTRACE(1);
+  TTRACE_CTA(2);
   // ---- partial tile -> shared memory P[BM][NP] (fp32), reusing the pipeline buffers
   float* P = reinterpret_cast<float*>(smem);
   {
@@ -353,11 +400,9 @@ __global__ void __launch_bounds__(K1_THREADS, 2)
       P[(row + 8) * NP + col + 1] = acc[j][3];
     }
   }
-  const double ss_cta = block_sum(ssd, red);
-  float* Gs = P + K1_BM * NP;            // r x r Gram partial of this CTA's rows
-  float* Ym = Gs + rr;                   // my reduced rows [rpc][r]
+  const float2 ss_cta = ff_block_sum(ssh, ssl, redf);
   if (tid == 0) {
-    ss_sh = ss_cta;
+    a.xx_part[(size_t)rt * nsplit + crank] = ss_cta;    // one partial of ||x||^2 per CTA
     if (timeout_flag) a.ctl->latched = 5;
   }
   cluster_sync();
@@ -370,116 +415,31 @@ __global__ void __launch_bounds__(K1_THREADS, 2)
     const int lr = e / r, c = e % r;
     const int row = rbeg + lr;
     const float s = dsmem_sum8(Pbase + (uint32_t)(row * NP + c) * 4u, nsplit);
-    Ym[lr * r + c] = s;
     if (m0 + row < a.M) a.Y[(long long)(m0 + row) * r + c] = s;
   }
-  __syncthreads();
-  for (int e = tid; e < rr; e += K1_THREADS) {
-    const int i = e / r, j = e % r;
-    float s = 0.f;
-    for (int lr = 0; lr < rpc; ++lr) s = fmaf(Ym[lr * r + i], Ym[lr * r + j], s);
-    Gs[e] = s;
-  }
-  cluster_sync();
-  if (crank == 0) {
-    const uint32_t Gbase = smem_u32(Gs);
-    for (int e = tid; e < rr; e += K1_THREADS) {
-      float v[8];
-#pragma unroll
-      for (int q = 0; q < 8; ++q) v[q] = (q < nsplit) ? dsmem_ld_f32(dsmem_addr(Gbase + (uint32_t)e * 4u, q)) : 0.f;
-      float hi = 0.f, lo = 0.f;
-#pragma unroll
-      for (int q = 0; q < 8; ++q) two_sum_acc(hi, lo, v[q]);
-      a.gram_part[(size_t)rt * rr + e] = hi + lo;
-    }
-    if (tid < 32) {
-      const uint32_t sb = smem_u32(&ss_sh);
-      double v = (tid < nsplit) ? dsmem_ld_f64(dsmem_addr(sb, tid)) : 0.0;
-      v = warp_sum(v);
-      if (tid == 0) a.xx_part[rt] = v;
-    }
-  }
-  cluster_sync();   // peers' shared memory stays valid until rank 0 has read it
+  cluster_sync();   // peers' shared memory stays valid until every rank has read it
+  TTRACE_CTA(3);
   if (tr0) TTRACE(3);
 }
 
 // ================================================================ K1b: r x r factor
-// A cluster of KB_CLUSTER CTAs.  Every CTA sums the Gram partials (W1), factors the scaled
-// Gram D W1 D = L L^T (FP32, one warp) and forms T1 = D L^{-T} (blocked triangular
-// inverse); CTA q then computes Q1 = Y T1 for its share of the rows (rounded to the
-// ingest type: the values that multiply X in the env kernel) and the Gram partial of
-// those rows on tensor cores (exact products).  Rank 0 reduces W2 = Q1^T Q1 through
-// distributed shared memory and forms Nx = W2^{-1} - I = -D2 + D2^2 - D2^3 (D2 = W2 - I).
+// A cluster of KB_CLUSTER CTAs; CTA q owns rows [q*nrows, (q+1)*nrows) of Y.
+//  1. Gram partial of my rows (FP32, 4 x 4 register blocks), W1 = the ranks' partials
+//     summed in rank order by every rank through distributed shared memory.
+//  2. Every rank factors the scaled Gram D W1 D = L L^T (FP32, one warp).
+//  3. Q1 = Y D L^{-T}: each thread forward-substitutes whole rows, z = L^{-1} (D y),
+//     and rounds them to the ingest type (the values that multiply X in the env kernel).
+//  4. W2 = Q1^T Q1 of the rounded rows on tensor cores (exact products), summed over the
+//     ranks; rank q forms rows of Nx = W2^{-1} - I = -D2 + D2^2 - D2^3 (D2 = W2 - I).
 // A failed factorisation (scaled pivot <= 1e-4: rank-deficient or badly conditioned Y)
 // takes the FP64 Householder QR of Y on rank 0 instead.
 constexpr int K1B_THREADS = 256;
 constexpr int KB_CLUSTER = 8;
 
-// C = alpha * A B for n x n row-major shared-memory matrices (leading dims la, lb, lc), all threads
-__device__ __forceinline__ void smem_mm(float* C, int lc, const float* A, int la, const float* B, int lb, int n,
-                                       float alpha) {
-  for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
-    const int i = e / n, j = e % n;
-    float s0 = 0.f, s1 = 0.f;
-    int k = 0;
-    for (; k + 1 < n; k += 2) {
-      s0 = fmaf(A[i * la + k], B[k * lb + j], s0);
-      s1 = fmaf(A[i * la + k + 1], B[(k + 1) * lb + j], s1);
-    }
-    if (k < n) s0 = fmaf(A[i * la + k], B[k * lb + j], s0);
-    C[i * lc + j] = alpha * (s0 + s1);
-  }
-}
-
-// Inverse of a lower-triangular n x n matrix (n = 32 or 64, identity-padded), blocked and
-// log-depth: 4 x 4 diagonal blocks by forward substitution, then for block widths
-// b = 4, 8, ... the off-diagonal block of [[A,0],[B,C]]^{-1} is -C^{-1} B A^{-1}.
-// X (n x n, ld n+1) receives the inverse; T is n/2 x n/2 scratch per block pair.
-__device__ void tri_lower_inverse(const float* L, int ldl, int n, float* X, float* T) {
-  const int ldx = n + 1;
-  for (int e = threadIdx.x; e < n * n; e += blockDim.x) X[(e / n) * ldx + e % n] = 0.f;
-  __syncthreads();
-  // 4 x 4 diagonal blocks: thread (blk, c) forward-substitutes column c
-  for (int e = threadIdx.x; e < (n / 4) * 4; e += blockDim.x) {
-    const int blk = e / 4, c = e % 4, o = blk * 4;
-    float x[4];
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      float s = (i == c) ? 1.f : 0.f;
-#pragma unroll
-      for (int k = 0; k < i; ++k) s = fmaf(-L[(o + i) * ldl + o + k], x[k], s);
-      x[i] = (i >= c) ? s / L[(o + i) * ldl + o + i] : 0.f;
-    }
-#pragma unroll
-    for (int i = 0; i < 4; ++i) X[(o + i) * ldx + o + c] = x[i];
-  }
-  __syncthreads();
-  for (int b = 4; b < n; b *= 2) {
-    const int npair = n / (2 * b);
-    // T = B A^{-1}  (B = L[o+b.., o..], A^{-1} = X[o.., o..]) for every pair
-    for (int e = threadIdx.x; e < npair * b * b; e += blockDim.x) {
-      const int pr = e / (b * b), i = (e / b) % b, j = e % b, o = pr * 2 * b;
-      float s = 0.f;
-      for (int k = j; k < b; ++k) s = fmaf(L[(o + b + i) * ldl + o + k], X[(o + k) * ldx + o + j], s);
-      T[pr * b * b + i * b + j] = s;
-    }
-    __syncthreads();
-    // X21 = -C^{-1} T
-    for (int e = threadIdx.x; e < npair * b * b; e += blockDim.x) {
-      const int pr = e / (b * b), i = (e / b) % b, j = e % b, o = pr * 2 * b;
-      float s = 0.f;
-      for (int k = 0; k <= i; ++k) s = fmaf(X[(o + b + i) * ldx + o + b + k], T[pr * b * b + k * b + j], s);
-      X[(o + b + i) * ldx + o + j] = -s;
-    }
-    __syncthreads();
-  }
-}
-
 struct FactorArgs {
   const float* Y;         // M x r
-  const float* gram_part; // [nrt][r*r]
-  const double* xx_part;  // [nrt]
-  int nrt, M, r;
+  const float2* xx_part;  // [nxx] float-float partials of ||x||^2
+  int nxx, M, r;
   void* Qh;               // M x NP ingest-type Q1 (columns >= r zero)
   float* Qst;             // state: Q1 (M x r) as float
   float* W2st;            // state: W2 (r x r)
@@ -491,65 +451,136 @@ struct FactorArgs {
 
 // rows of Y handled by one CTA of the factor cluster
 __host__ __device__ constexpr int k1b_rows(int M) { return ((M + KB_CLUSTER - 1) / KB_CLUSTER + 15) / 16 * 16; }
-// dynamic shared memory: Y rows (padded r+1) | Q1 rows (ingest type, padded NP+8) |
-// Gram partial (NP x NP) | triangular-inverse and Nx scratch
+// row groups of the Gram partial: 4 x 4 blocks of an NP x NP Gram per thread
+__host__ __device__ constexpr int k1b_rgroups(int np) {
+  return K1B_THREADS / ((np / 4) * (np / 4)) > 0 ? K1B_THREADS / ((np / 4) * (np / 4)) : 1;
+}
+// dynamic shared memory: Y rows (fp32, stride NP+4) | Q1 rows (ingest type, stride NP+8) |
+// Gram partials of the row groups | this rank's Gram partial (W1, later W2)
 __host__ __device__ constexpr size_t k1b_smem_bytes(int M, int r, int np) {
-  return (size_t)k1b_rows(M) * (r + 1) * 4 + (size_t)(k1b_rows(M) + 16) * (np + 8) * 2 + (size_t)np * np * 4 +
-         (size_t)(2 * 64 * 65 + 32 * 32) * 4 + 256;
+  return (size_t)k1b_rows(M) * (np + 4) * 4 + (size_t)(k1b_rows(M) + 16) * (np + 8) * 2 +
+         (size_t)k1b_rgroups(np) * np * np * 4 + (size_t)np * np * 4 + 256 + 0 * r;
 }
 
 template <typename TX, int NP>
 __global__ void __launch_bounds__(K1B_THREADS) k_fast_factor(FactorArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ float W[64 * 64];
-  __shared__ float L[64 * 65];
+  constexpr int LDY = NP + 4, LQ = NP + 8, LDT = NP + 4;
+  constexpr int NB = NP / 4, NBLK = NB * NB, NRG = k1b_rgroups(NP);
+  __shared__ float W[64 * 64];             // W1, then W2 (r x r)
+  __shared__ __align__(16) float LT[64 * 68];   // L^T: LT[k*LDT + i] = L[i][k] (zero above)
   __shared__ float dsc[64];
+  __shared__ float invd[64];               // 1 / L[i][i]
   __shared__ double red[32];
-  __shared__ int flags[2];     // [0] non-finite, [1] factorisation failed
+  __shared__ int flags[2];                 // [0] non-finite, [1] factorisation failed
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int r = a.r, rr = r * r, LD = r + 1;
+  const int r = a.r, rr = r * r;
   const uint32_t crank = cluster_rank();
   const int nrows = k1b_rows(a.M);
   const int row0 = (int)crank * nrows;
   const int myrows = (a.M - row0 < nrows) ? (a.M - row0 > 0 ? a.M - row0 : 0) : nrows;
-  constexpr int LQ = NP + 8;
-  float* Ys = reinterpret_cast<float*>(smem);                         // [nrows][r+1]
-  TX* Qs = reinterpret_cast<TX*>(Ys + (size_t)nrows * LD);            // [nrows+16][LQ]
-  float* Gp = reinterpret_cast<float*>(Qs + (size_t)(nrows + 16) * LQ);   // [NP][NP]
-  float* scr = Gp + NP * NP;                                          // inverse / Nx scratch
+  float* Ys = reinterpret_cast<float*>(smem);                               // [nrows][LDY]
+  TX* Qs = reinterpret_cast<TX*>(Ys + (size_t)nrows * LDY);                 // [nrows+16][LQ]
+  float* Gr = reinterpret_cast<float*>(Qs + (size_t)(nrows + 16) * LQ);     // [NRG][NP*NP]
+  float* Wp = Gr + NRG * NP * NP;                                          // [NP*NP]
   pdl_wait();
   pdl_trigger();
   TTRACE(10);
-  // my rows of Y (coalesced; independent of the factor)
-  for (int e = tid; e < myrows * r; e += K1B_THREADS) Ys[(e / r) * LD + e % r] = a.Y[(long long)row0 * r + e];
-  for (int e = tid; e < rr; e += K1B_THREADS) {
-    float hi = 0.f, lo = 0.f;
-    for (int b0 = 0; b0 < a.nrt; b0 += 8) {
-      float v[8];
-#pragma unroll
-      for (int q = 0; q < 8; ++q) v[q] = (b0 + q < a.nrt) ? a.gram_part[(size_t)(b0 + q) * rr + e] : 0.f;
-#pragma unroll
-      for (int q = 0; q < 8; ++q) two_sum_acc(hi, lo, v[q]);
+  // ---- my rows of Y (asynchronous copies; padding columns r..NP-1 zero)
+  if ((r & 3) == 0) {
+    const int cpr = r / 4;
+    for (int e = tid; e < myrows * cpr; e += K1B_THREADS) {
+      const int row = e / cpr, ch = e % cpr;
+      cp_async16(smem_u32(Ys + row * LDY + ch * 4), a.Y + (long long)(row0 + row) * r + ch * 4, 16u);
     }
-    W[e] = hi + lo;
+  } else {
+    for (int e = tid; e < myrows * r; e += K1B_THREADS)
+      cp_async4(smem_u32(Ys + (e / r) * LDY + e % r), a.Y + (long long)row0 * r + e);
   }
+  cp_async_commit();
+  if (r < NP)
+    for (int e = tid; e < myrows * (NP - r); e += K1B_THREADS) Ys[(e / (NP - r)) * LDY + r + e % (NP - r)] = 0.f;
   if (warp == 0) {
-    double xs = 0.0;
-    for (int b = lane; b < a.nrt; b += 32) xs += a.xx_part[b];
-    xs = warp_sum(xs);
+    float xh = 0.f, xl = 0.f;
+    for (int b0 = lane; b0 < a.nxx; b0 += 32 * 8) {
+      float2 v[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) v[q] = (b0 + 32 * q < a.nxx) ? a.xx_part[b0 + 32 * q] : make_float2(0.f, 0.f);
+#pragma unroll
+      for (int q = 0; q < 8; ++q) ff_add(xh, xl, v[q].x, v[q].y);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const float bh = __shfl_down_sync(0xffffffffu, xh, o), bl = __shfl_down_sync(0xffffffffu, xl, o);
+      ff_add(xh, xl, bh, bl);
+    }
     if (lane == 0) {
+      const double xs = (double)xh + (double)xl;
       flags[0] = !isfinite(xs);
       flags[1] = 0;
       if (crank == 0) a.ctl->xx = xs;
     }
   }
+  cp_async_wait<0>();
+  __syncthreads();
+  // ---- 1. Gram partial: thread (row group, 4 x 4 block); row groups summed in order
+  if (tid < NRG * NBLK) {
+    const int blk = tid % NBLK, rg = tid / NBLK, ib = blk / NB, jb = blk % NB;
+    float acc[4][4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int w = 0; w < 4; ++w) acc[u][w] = 0.f;
+    for (int row = rg; row < myrows; row += NRG) {
+      const float4 yi = *reinterpret_cast<const float4*>(Ys + row * LDY + 4 * ib);
+      const float4 yj = *reinterpret_cast<const float4*>(Ys + row * LDY + 4 * jb);
+      const float vi[4] = {yi.x, yi.y, yi.z, yi.w}, vj[4] = {yj.x, yj.y, yj.z, yj.w};
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int w = 0; w < 4; ++w) acc[u][w] = fmaf(vi[u], vj[w], acc[u][w]);
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int w = 0; w < 4; ++w) Gr[rg * NP * NP + (4 * ib + u) * NP + 4 * jb + w] = acc[u][w];
+  }
+  __syncthreads();
+  for (int e = tid; e < NP * NP; e += K1B_THREADS) {
+    float sum = 0.f;
+#pragma unroll
+    for (int g = 0; g < NRG; ++g) sum += Gr[g * NP * NP + e];
+    Wp[e] = sum;
+  }
+  cluster_sync();
+  {
+    const uint32_t wb = smem_u32(Wp);
+    for (int e0 = tid; e0 < rr; e0 += 4 * K1B_THREADS) {
+      float v[4][KB_CLUSTER];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int e = e0 + u * K1B_THREADS;
+        const uint32_t la = wb + (uint32_t)((e / r) * NP + e % r) * 4u;
+#pragma unroll
+        for (int q = 0; q < KB_CLUSTER; ++q) v[u][q] = e < rr ? dsmem_ld_f32(dsmem_addr(la, (uint32_t)q)) : 0.f;
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        float hi = 0.f, lo = 0.f;
+#pragma unroll
+        for (int q = 0; q < KB_CLUSTER; ++q) two_sum_acc(hi, lo, v[u][q]);
+        if (e0 + u * K1B_THREADS < rr) W[e0 + u * K1B_THREADS] = hi + lo;
+      }
+    }
+  }
+  cluster_arrive();     // my partial may be released once every rank has read it (wait below)
   __syncthreads();
   for (int e = tid; e < rr; e += K1B_THREADS)
     if (!isfinite(W[e])) flags[0] = 1;
-  if (tid < r) {
-    const float d = W[tid * r + tid];
+  if (tid < 64) {
+    const float d = tid < r ? W[tid * r + tid] : 0.f;
     dsc[tid] = d > 0.f ? rsqrtf(d) : 0.f;
-    if (!(d > 0.f)) flags[1] = 1;
+    if (tid < r && !(d > 0.f)) flags[1] = 1;
   }
   __syncthreads();
   if (crank == 0 && tid == 0) {
@@ -557,9 +588,14 @@ __global__ void __launch_bounds__(K1B_THREADS) k_fast_factor(FactorArgs a) {
     a.ctl->skip = flags[0];
     if (flags[0]) a.ctl->latched = 4;
   }
-  if (flags[0]) return;     // uniform across the cluster (same data): no cluster barrier follows
+  if (flags[0]) {           // uniform across the cluster (identical W1 and ||x||^2)
+    cluster_wait();
+    return;
+  }
   TTRACE(11);
-  // ---- Cholesky of the scaled Gram: D W D = L L^T
+  // ---- 2. Cholesky of the scaled Gram: D W1 D = L L^T, stored transposed (LT)
+  for (int e = tid; e < NP * LDT; e += K1B_THREADS) LT[e] = 0.f;
+  __syncthreads();
   if (!flags[1]) {
     if constexpr (NP <= 32) {
       if (warp == 0) {
@@ -570,7 +606,8 @@ __global__ void __launch_bounds__(K1B_THREADS) k_fast_factor(FactorArgs a) {
         int ok = 1;
 #pragma unroll
         for (int j = 0; j < 32; ++j) {
-          const float wj = (lane < r && j < r) ? W[lane * r + j] * di * dsc[j] : (lane == j ? 1.f : 0.f);
+          // W1 is symmetric: W[j][lane] = W[lane][j], read along the row (conflict-free)
+          const float wj = (lane < r && j < r) ? W[j * r + lane] * di * dsc[j] : (lane == j ? 1.f : 0.f);
           float s0 = wj, s1 = 0.f, s2 = 0.f, s3 = 0.f;
 #pragma unroll
           for (int k = 0; k < j; k += 4) {
@@ -584,20 +621,20 @@ __global__ void __launch_bounds__(K1B_THREADS) k_fast_factor(FactorArgs a) {
           if (!(piv > 1e-4f)) ok = 0;
           const float rl = rsqrtf(piv > 0.f ? piv : 1.f);
           l[j] = (lane == j) ? piv * rl : (lane > j ? sv * rl : 0.f);
+          if (lane == j) invd[j] = rl;
         }
 #pragma unroll
         for (int k = 0; k < 32; ++k)
-          if (lane < r && k < r) L[lane * LD + k] = l[k];
+          if (lane < r && k < r) LT[k * LDT + lane] = l[k];
         if (lane == 0) flags[1] = ok ? 0 : 1;
       }
     } else {
-      for (int e = tid; e < rr; e += K1B_THREADS) {
-        const int i = e / r, j = e % r;
-        L[i * LD + j] = W[e] * dsc[i] * dsc[j];
-      }
+      float* Lw = W;                           // in place (W1 is not needed afterwards)
+      const int LD = r;
+      for (int e = tid; e < rr; e += K1B_THREADS) W[e] *= dsc[e / r] * dsc[e % r];
       __syncthreads();
       for (int j = 0; j < r; ++j) {
-        const float piv = L[j * LD + j];
+        const float piv = Lw[j * LD + j];
         if (!(piv > 1e-4f)) {
           if (tid == 0) flags[1] = 1;
           break;                      // uniform
@@ -605,14 +642,21 @@ __global__ void __launch_bounds__(K1B_THREADS) k_fast_factor(FactorArgs a) {
         const float rl = rsqrtf(piv);
         for (int e = tid; e < rr; e += K1B_THREADS) {
           const int i = e / r, k = e % r;
-          if (i > j && k > j && k <= i) L[i * LD + k] -= L[i * LD + j] * L[k * LD + j] / piv;
+          if (i > j && k > j && k <= i) Lw[i * LD + k] -= Lw[i * LD + j] * Lw[k * LD + j] / piv;
         }
         __syncthreads();
-        if (tid >= j && tid < r) L[tid * LD + j] *= rl;
+        if (tid >= j && tid < r) Lw[tid * LD + j] *= rl;
+        if (tid == j) invd[j] = rl;
         __syncthreads();
       }
+      if (!flags[1])
+        for (int e = tid; e < rr; e += K1B_THREADS) {
+          const int i = e / r, k = e % r;
+          if (k <= i) LT[k * LDT + i] = Lw[i * LD + k];
+        }
     }
   }
+  cluster_wait();           // every rank has read W1's partials
   __syncthreads();
   TTRACE(12);
   TX* Qh = (TX*)a.Qh;
@@ -620,163 +664,139 @@ __global__ void __launch_bounds__(K1B_THREADS) k_fast_factor(FactorArgs a) {
   if (fb) {
     if (crank == 0) householder_cta<float, float>(a.Y, a.M, r, r, a.hh_work, a.Qfb, r, red);
     cluster_sync();                   // Qfb complete before the other ranks read it
-    for (int e = tid; e < myrows * r; e += K1B_THREADS) Ys[(e / r) * LD + e % r] = a.Qfb[(long long)row0 * r + e];
   }
-  // T1 = D L^{-T} (identity when the Householder Q is used)
-  float* T1 = W;
-  if (!fb) {
-    const int n = r <= 32 ? 32 : 64;
-    float* Lp = scr;                       // n x (n+1)
-    float* Xi = Lp + n * (n + 1);          // n x (n+1)
-    float* Tt = Xi + n * (n + 1);          // (n/2)^2
-    for (int e = tid; e < n * n; e += K1B_THREADS) {
-      const int i = e / n, j = e % n;
-      Lp[i * (n + 1) + j] = (i < r && j < r) ? (j <= i ? L[i * LD + j] : 0.f) : (i == j ? 1.f : 0.f);
-    }
-    __syncthreads();
-    tri_lower_inverse(Lp, n + 1, n, Xi, Tt);
-    for (int e = tid; e < rr; e += K1B_THREADS) {
-      const int k = e / r, c = e % r;
-      T1[e] = dsc[k] * Xi[c * (n + 1) + k];    // (D L^{-T})[k][c] = d_k (L^{-1})[c][k]
-    }
-  } else {
-    for (int e = tid; e < rr; e += K1B_THREADS) T1[e] = ((e / r) == (e % r)) ? 1.f : 0.f;
-  }
-  __syncthreads();
-  // Q1 rows = Y rows T1: 4 x 4 register blocks; a thread takes rows br + u*nbr, so the
-  // lanes of a warp read consecutive padded rows (stride r+1: conflict-free)
-  {
-    const int nbc = (r + 3) / 4;
-    const int nbr = (myrows + 3) / 4;
-    for (int task = tid; task < nbr * nbc; task += K1B_THREADS) {
-      const int br = task % nbr, bc = task / nbr;      // consecutive threads: consecutive row blocks
-      float q[4][4];
+  // ---- 3. Q1 rows: z = L^{-1} (D y) by forward substitution (Householder Q: z = q)
+  for (int row = tid; row < nrows + 16; row += K1B_THREADS) {
+    float z[NP];
+    if (row < myrows) {
+      if (!fb) {
 #pragma unroll
-      for (int u = 0; u < 4; ++u)
-#pragma unroll
-        for (int w = 0; w < 4; ++w) q[u][w] = 0.f;
-      const int kmax = fb ? r - 1 : ((4 * bc + 3 < r) ? 4 * bc + 3 : r - 1);
-      for (int k = 0; k <= kmax; ++k) {
-        float y[4], t[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) y[u] = (br + u * nbr < myrows) ? Ys[(br + u * nbr) * LD + k] : 0.f;
-#pragma unroll
-        for (int w = 0; w < 4; ++w) t[w] = (4 * bc + w < r) ? T1[k * r + 4 * bc + w] : 0.f;
-#pragma unroll
-        for (int u = 0; u < 4; ++u)
-#pragma unroll
-          for (int w = 0; w < 4; ++w) q[u][w] = fmaf(y[u], t[w], q[u][w]);
-      }
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int row = br + u * nbr;
-        if (row >= myrows) continue;
-#pragma unroll
-        for (int w = 0; w < 4; ++w) {
-          const int c = 4 * bc + w;
-          if (c < r) Qs[row * LQ + c] = from_acc<TX>(q[u][w]);
+        for (int c4 = 0; c4 < NP / 4; ++c4) {
+          const float4 y = *reinterpret_cast<const float4*>(Ys + row * LDY + 4 * c4);
+          z[4 * c4 + 0] = y.x * dsc[4 * c4 + 0];
+          z[4 * c4 + 1] = y.y * dsc[4 * c4 + 1];
+          z[4 * c4 + 2] = y.z * dsc[4 * c4 + 2];
+          z[4 * c4 + 3] = y.w * dsc[4 * c4 + 3];
         }
+#pragma unroll
+        for (int k = 0; k < NP; ++k) {
+          if (k < r) {
+            z[k] *= invd[k];
+#pragma unroll
+            for (int i4 = (k + 1) / 4; i4 < NP / 4; ++i4) {
+              const float4 lv = *reinterpret_cast<const float4*>(LT + k * LDT + 4 * i4);
+              if (4 * i4 + 0 > k) z[4 * i4 + 0] = fmaf(-lv.x, z[k], z[4 * i4 + 0]);
+              if (4 * i4 + 1 > k) z[4 * i4 + 1] = fmaf(-lv.y, z[k], z[4 * i4 + 1]);
+              if (4 * i4 + 2 > k) z[4 * i4 + 2] = fmaf(-lv.z, z[k], z[4 * i4 + 2]);
+              if (4 * i4 + 3 > k) z[4 * i4 + 3] = fmaf(-lv.w, z[k], z[4 * i4 + 3]);
+            }
+          } else {
+            z[k] = 0.f;
+          }
+        }
+      } else {
+#pragma unroll
+        for (int c = 0; c < NP; ++c) z[c] = c < r ? a.Qfb[(long long)(row0 + row) * r + c] : 0.f;
       }
+    } else {
+#pragma unroll
+      for (int c = 0; c < NP; ++c) z[c] = 0.f;     // rows past my share: read by the last k-step
     }
-    // zero: padding columns and the rows past my share (read by the last k-step below)
-    for (int e = tid; e < (nrows + 16) * LQ; e += K1B_THREADS) {
-      const int row = e / LQ, c = e % LQ;
-      if (row >= myrows || c >= r) Qs[e] = from_acc<TX>(0.f);
+    // rounded row -> shared memory (W2 operand; written out below)
+#pragma unroll
+    for (int c8 = 0; c8 < NP / 8; ++c8) {
+      uint32_t w[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const TX lo = from_acc<TX>(z[8 * c8 + 2 * q]), hi = from_acc<TX>(z[8 * c8 + 2 * q + 1]);
+        w[q] = (uint32_t)tx_bits(lo) | ((uint32_t)tx_bits(hi) << 16);
+      }
+      *reinterpret_cast<uint4*>(Qs + row * LQ + 8 * c8) = make_uint4(w[0], w[1], w[2], w[3]);
     }
   }
   __syncthreads();
-  // write my Q1 rows (coalesced) in the ingest type and as float
-  for (int e = tid; e < myrows * NP; e += K1B_THREADS) {
-    const int row = e / NP, c = e % NP;
-    const TX h = Qs[row * LQ + c];
-    Qh[(long long)(row0 + row) * NP + c] = h;
-    if (c < r) a.Qst[(long long)(row0 + row) * r + c] = Cvt<TX>::f(h);
+  // my rows of Q1, coalesced: ingest-type copy (16-byte chunks) and FP32 state
+  for (int e = tid; e < myrows * (NP / 8); e += K1B_THREADS) {
+    const int row = e / (NP / 8), c8 = e % (NP / 8);
+    *reinterpret_cast<uint4*>(Qh + (long long)(row0 + row) * NP + 8 * c8) =
+        *reinterpret_cast<const uint4*>(Qs + row * LQ + 8 * c8);
   }
+  for (int e = tid; e < myrows * r; e += K1B_THREADS)
+    a.Qst[(long long)row0 * r + e] = Cvt<TX>::f(Qs[(e / r) * LQ + e % r]);
   TTRACE(13);
-  // Gram partial of my rows on tensor cores: warp w takes k-steps w, w+8, ...
+  // ---- 4. W2 partial of my rows on tensor cores: warp w owns output tiles w, w+8, ...
   {
     constexpr int MT = NP / 16, NTT = NP / 8;
-    const int nw = K1B_THREADS / 32;
     const int ksteps = (myrows + 15) / 16;
-    float acc[MT][NTT][4];
-#pragma unroll
-    for (int m = 0; m < MT; ++m)
-#pragma unroll
-      for (int n = 0; n < NTT; ++n) acc[m][n][0] = acc[m][n][1] = acc[m][n][2] = acc[m][n][3] = 0.f;
-    for (int ks = warp; ks < ksteps; ks += nw) {
-      const int k0 = ks * 16;
-#pragma unroll
-      for (int m = 0; m < MT; ++m) {
-        uint32_t af[4];
-        {
-          const int row = k0 + (lane & 7) + ((lane >> 4) << 3);
-          const int col = m * 16 + ((lane >> 3) & 1) * 8;
-          ldsm_x4_t(smem_u32(Qs + row * LQ + col), af[0], af[1], af[2], af[3]);
-        }
-#pragma unroll
-        for (int p = 0; p < NTT / 2; ++p) {
-          uint32_t b0, b1, b2, b3;
-          const int row = k0 + (lane & 7) + (((lane >> 3) & 1) << 3);
-          const int col = p * 16 + ((lane >> 4) << 3);
-          ldsm_x4_t(smem_u32(Qs + row * LQ + col), b0, b1, b2, b3);
-          mma16816<TX>(acc[m][2 * p], af, b0, b1);
-          mma16816<TX>(acc[m][2 * p + 1], af, b2, b3);
-        }
-      }
-    }
-    // sum the warps' fragments in a fixed order into Gp
-    for (int e = tid; e < NP * NP; e += K1B_THREADS) Gp[e] = 0.f;
-    __syncthreads();
     const int g = lane >> 2, t4 = lane & 3;
-    for (int w = 0; w < nw; ++w) {
-      if (warp == w) {
-#pragma unroll
-        for (int m = 0; m < MT; ++m)
-#pragma unroll
-          for (int n = 0; n < NTT; ++n) {
-            const int row = m * 16 + g, col = n * 8 + 2 * t4;
-            Gp[row * NP + col] += acc[m][n][0];
-            Gp[row * NP + col + 1] += acc[m][n][1];
-            Gp[(row + 8) * NP + col] += acc[m][n][2];
-            Gp[(row + 8) * NP + col + 1] += acc[m][n][3];
-          }
+    for (int tile = warp; tile < MT * NTT; tile += K1B_THREADS / 32) {
+      const int m = tile / NTT, n = tile % NTT;
+      float acc[4] = {0.f, 0.f, 0.f, 0.f};
+      for (int ks = 0; ks < ksteps; ++ks) {
+        const int k0 = ks * 16;
+        uint32_t af[4], b0, b1;
+        ldsm_x4_t(smem_u32(Qs + (k0 + (lane & 7) + ((lane >> 4) << 3)) * LQ + m * 16 + ((lane >> 3) & 1) * 8), af[0],
+                  af[1], af[2], af[3]);
+        ldsm_x2_t(smem_u32(Qs + (k0 + (lane & 7) + (((lane >> 3) & 1) << 3)) * LQ + n * 8), b0, b1);
+        mma16816<TX>(acc, af, b0, b1);
       }
-      __syncthreads();
+      const int row = m * 16 + g, col = n * 8 + 2 * t4;
+      Wp[row * NP + col] = acc[0];
+      Wp[row * NP + col + 1] = acc[1];
+      Wp[(row + 8) * NP + col] = acc[2];
+      Wp[(row + 8) * NP + col + 1] = acc[3];
     }
   }
   cluster_sync();
-  TTRACE(14);
-  if (crank == 0) {
-    // W2 = sum of the ranks' partials (fixed order), then Nx
-    const uint32_t gb = smem_u32(Gp);
-    for (int e = tid; e < rr; e += K1B_THREADS) {
-      const int i = e / r, j = e % r;
-      float v[8];
+  // W2 = the ranks' partials in rank order (every rank)
+  {
+    const uint32_t wb = smem_u32(Wp);
+    for (int e0 = tid; e0 < rr; e0 += 4 * K1B_THREADS) {
+      float v[4][KB_CLUSTER];
 #pragma unroll
-      for (int q = 0; q < 8; ++q)
-        v[q] = (q < KB_CLUSTER) ? dsmem_ld_f32(dsmem_addr(gb + (uint32_t)(i * NP + j) * 4u, q)) : 0.f;
-      float hi = 0.f, lo = 0.f;
+      for (int u = 0; u < 4; ++u) {
+        const int e = e0 + u * K1B_THREADS;
+        const uint32_t la = wb + (uint32_t)((e / r) * NP + e % r) * 4u;
 #pragma unroll
-      for (int q = 0; q < 8; ++q) two_sum_acc(hi, lo, v[q]);
-      W[e] = hi + lo;
+        for (int q = 0; q < KB_CLUSTER; ++q) v[u][q] = e < rr ? dsmem_ld_f32(dsmem_addr(la, (uint32_t)q)) : 0.f;
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        float hi = 0.f, lo = 0.f;
+#pragma unroll
+        for (int q = 0; q < KB_CLUSTER; ++q) two_sum_acc(hi, lo, v[u][q]);
+        if (e0 + u * K1B_THREADS < rr) W[e0 + u * K1B_THREADS] = hi + lo;
+      }
     }
-    __syncthreads();
-    float* D2 = L;                                      // r x r
-    float* U = scr;                                     // D2^2
-    float* V = U + rr;                                  // D2^3
-    for (int e = tid; e < rr; e += K1B_THREADS) {
-      a.W2st[e] = W[e];
-      D2[e] = W[e] - ((e / r) == (e % r) ? 1.f : 0.f);
-    }
-    __syncthreads();
-    smem_mm(U, r, D2, r, D2, r, r, 1.f);
-    __syncthreads();
-    smem_mm(V, r, D2, r, U, r, r, 1.f);
-    __syncthreads();
-    for (int e = tid; e < rr; e += K1B_THREADS) a.Nx[e] = -D2[e] + U[e] - V[e];
-    if (tid == 0 && fb) a.ctl->fallback[0] = 1;
   }
-  cluster_sync();   // peers' partials stay valid until rank 0 has read them
+  cluster_arrive();   // peers may leave once every rank has read my partial (wait at the end)
+  __syncthreads();
+  TTRACE(14);
+  // ---- rows [i0, i1) of Nx = -D2 + D2^2 - D2^3 (D2 = W2 - I): U = D2 rows x D2, V = U x D2
+  {
+    const int rpb = (r + KB_CLUSTER - 1) / KB_CLUSTER;
+    const int i0 = (int)crank * rpb, i1 = (i0 + rpb < r) ? i0 + rpb : r;
+    const int nr = i1 > i0 ? i1 - i0 : 0;
+    float* U = Gr;                   // nr x r
+    for (int e = tid; e < nr * r; e += K1B_THREADS) {
+      const int i = i0 + e / r, j = e % r;
+      float sum = 0.f;
+      for (int k = 0; k < r; ++k)
+        sum = fmaf(W[i * r + k] - (i == k ? 1.f : 0.f), W[k * r + j] - (k == j ? 1.f : 0.f), sum);
+      U[e] = sum;
+    }
+    __syncthreads();
+    for (int e = tid; e < nr * r; e += K1B_THREADS) {
+      const int i = i0 + e / r, j = e % r;
+      float v = 0.f;
+      for (int k = 0; k < r; ++k) v = fmaf(U[(e / r) * r + k], W[k * r + j] - (k == j ? 1.f : 0.f), v);
+      const float d2 = W[i * r + j] - (i == j ? 1.f : 0.f);
+      a.Nx[i * r + j] = -d2 + U[e] - v;
+      a.W2st[i * r + j] = W[i * r + j];
+    }
+    if (tid == 0 && crank == 0 && fb) a.ctl->fallback[0] = 1;
+  }
+  cluster_wait();
   TTRACE(15);
 }
 
@@ -797,7 +817,7 @@ struct EnvArgs {
   float* Cst;           // state: F (r x J)
   void* Chst;           // state: scaled ingest-type copy of F (r x J)
   int* ch_shift;        // state: power-of-two scale exponent of Chst
-  double* cc_part;      // [column tiles]
+  float2* cc_part;      // [CTAs] float-float partials of ||x^||^2
   unsigned* counter;    // self-resetting
   Ctl* ctl;
   // previous state (copied into the new one when the step is skipped)
@@ -813,8 +833,8 @@ struct EnvArgs {
 
 template <int NP>
 constexpr size_t k2_smem_bytes(int rch, int r) {
-  // X block (2 x rch x 128 B) | Q1 tile | partial tile P (BN x NP) | my columns F | Nx
-  return 1024 + (size_t)rch * 256 + (size_t)rch * (NP + 8) * 2 + (size_t)K2_BN * NP * 4 +
+  // X block (2 x rch x 128 B) | Q1 tile | partial tile P (BN x (NP+8)) | my columns F | Nx
+  return 1024 + (size_t)rch * 256 + (size_t)rch * (NP + 8) * 2 + (size_t)K2_BN * (NP + 8) * 4 +
          (size_t)K2_BN * (r + 1) * 4 + (size_t)r * r * 4 + 64;
 }
 
@@ -827,13 +847,13 @@ __global__ void __launch_bounds__(K2_THREADS, 2)
   const int rch = a.rch, r = a.r, rr = r * r;
   const uint32_t xsub0 = smem_u32(smem), xsub1 = xsub0 + (uint32_t)rch * 128;   // two swizzled boxes
   TX* sQ = reinterpret_cast<TX*>(smem + (size_t)rch * 256);           // [rch][NP+8]
-  float* P = reinterpret_cast<float*>(sQ + (size_t)rch * (NP + 8));  // [BN][NP]
+  constexpr int LDP = NP + 8;                                        // float2 stores: 2 wavefronts
+  float* P = reinterpret_cast<float*>(sQ + (size_t)rch * (NP + 8));  // [BN][NP+8]
   const int LDF = r + 1;                                             // padded: conflict-free
-  float* sF = P + K2_BN * NP;                                        // [BN][r+1] (my columns)
+  float* sF = P + K2_BN * LDP;                                       // [BN][r+1] (my columns)
   float* sN = sF + K2_BN * LDF;                                      // Nx
   __shared__ __align__(8) uint64_t xbar;
-  __shared__ double red[32];
-  __shared__ double cc_sh;
+  __shared__ float redf[64];
   __shared__ int last_flag;
   __shared__ int timeout_flag;
 
@@ -861,6 +881,14 @@ __global__ void __launch_bounds__(K2_THREADS, 2)
   pdl_wait();
   pdl_trigger();
   if (tr0) TTRACE(21);
+  const double xx = a.ctl->xx;     // ||x||^2 of this slice (factor kernel)
+  double sum_xx = 0.0, sum_ee = 0.0;  // running totals (read early; used by the last CTA)
+  long long tcount = 0;
+  if (tid == 0) {
+    sum_xx = a.ctl->sum_xx;
+    sum_ee = a.ctl->sum_ee;
+    tcount = a.ctl->t;
+  }
   if (a.ctl->skip) {
     // non-finite slice: the new state is the old one
     const long long nthr = (long long)gridDim.x * gridDim.y * K2_THREADS;
@@ -885,8 +913,8 @@ __global__ void __launch_bounds__(K2_THREADS, 2)
       const bool ok = gi < a.M;
       cp_async16(smem_u32(sQ + row * (NP + 8) + ch * 8), Qh + (ok ? (long long)gi * NP + ch * 8 : 0), ok ? 16u : 0u);
     }
+    for (int e = tid; e < rr; e += K2_THREADS) cp_async4(smem_u32(sN + e), a.Nx + e);
     cp_async_commit();
-    for (int e = tid; e < rr; e += K2_THREADS) sN[e] = a.Nx[e];
     cp_async_wait<0>();
   }
   if (!mbar_wait(smem_u32(&xbar), 0)) timeout_flag = 1;
@@ -923,10 +951,8 @@ __global__ void __launch_bounds__(K2_THREADS, 2)
     for (int j = 0; j < NT; ++j) {
       const int col = j * 8 + 2 * t4;
       const int row = warp * 16 + g;
-      P[row * NP + col] = acc[j][0];
-      P[row * NP + col + 1] = acc[j][1];
-      P[(row + 8) * NP + col] = acc[j][2];
-      P[(row + 8) * NP + col + 1] = acc[j][3];
+      *reinterpret_cast<float2*>(P + row * LDP + col) = make_float2(acc[j][0], acc[j][1]);
+      *reinterpret_cast<float2*>(P + (row + 8) * LDP + col) = make_float2(acc[j][2], acc[j][3]);
     }
   }
   if (tid == 0 && timeout_flag) a.ctl->latched = 5;
@@ -940,15 +966,31 @@ __global__ void __launch_bounds__(K2_THREADS, 2)
   const int nmy = je > jb ? je - jb : 0;
   {
     const uint32_t Pb = smem_u32(P);
-    for (int e = tid; e < nmy * r; e += K2_THREADS) {
-      const int jl = e / r, c = e % r;
-      sF[jl * LDF + c] = dsmem_sum8(Pb + (uint32_t)((jb + jl) * NP + c) * 4u, nq);
+    for (int e0 = tid; e0 < nmy * r; e0 += 4 * K2_THREADS) {
+      float v[4][8];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int e = e0 + u * K2_THREADS;
+        const int jl = e / r, c = e % r;
+        const uint32_t la = Pb + (uint32_t)((jb + jl) * LDP + c) * 4u;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) v[u][q] = (e < nmy * r && q < nq) ? dsmem_ld_f32(dsmem_addr(la, q)) : 0.f;
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int e = e0 + u * K2_THREADS;
+        if (e < nmy * r) {
+          float sum = 0.f;
+#pragma unroll
+          for (int q = 0; q < 8; ++q) sum += v[u][q];
+          sF[(e / r) * LDF + e % r] = sum;
+        }
+      }
     }
   }
   cluster_sync();   // every rank has read the peers' tiles
   if (tr0) TTRACE(25);
   // write F and its ingest-type copy (coalesced along j); ||x^||^2 of my columns
-  const double xx = a.ctl->xx;
   int shift = 0;
   if (a.is_half && xx > 0.0) {
     const float nrm = sqrtf((float)xx);
@@ -956,7 +998,7 @@ __global__ void __launch_bounds__(K2_THREADS, 2)
   }
   if (ct == 0 && crank == 0 && tid == 0) *a.ch_shift = shift;
   const float scale = ldexpf(1.0f, -shift);
-  double part = 0.0;
+  float ph = 0.f, pl = 0.f;     // float-float partial of ||x^||^2
   for (int e = tid; e < nmy * r; e += K2_THREADS) {
     const int c = e / nmy, jl = e % nmy;
     const long long gj = j0 + jb + jl;
@@ -966,43 +1008,44 @@ __global__ void __launch_bounds__(K2_THREADS, 2)
     // f_c * (f + Nx f)_c
     float g = f;
     for (int b = 0; b < r; ++b) g = fmaf(sN[c * r + b], sF[jl * LDF + b], g);
-    part += (double)(f * g);
+    two_sum_acc(ph, pl, f * g);
   }
-  const double cc_cta = block_sum(part, red);
-  if (tid == 0) cc_sh = cc_cta;
+  const float2 cc_cta = ff_block_sum(ph, pl, redf);
   if (tr0) TTRACE(26);
-  cluster_sync();
-  if (crank == 0 && tid < 32) {
-    const uint32_t cb = smem_u32(&cc_sh);
-    double v = (tid < nq) ? dsmem_ld_f64(dsmem_addr(cb, tid)) : 0.0;
-    v = warp_sum(v);
-    if (tid == 0) a.cc_part[ct] = v;
-  }
-  cluster_sync();
-  if (crank != 0) return;
-  __threadfence();
+  // one partial per CTA; the last CTA of the grid sums them in a fixed order
+  const int ncta = (int)(gridDim.x * gridDim.y);
   if (tid == 0) {
+    a.cc_part[(size_t)ct * nq + crank] = cc_cta;
+    __threadfence();
     const unsigned done = atomicAdd(a.counter, 1u);
-    last_flag = (done == gridDim.x - 1);
+    last_flag = (done == (unsigned)ncta - 1u);
   }
   __syncthreads();
   if (!last_flag) return;
   TTRACE(27);
   __threadfence();
-  double s = 0.0;
-  for (int b = tid; b < (int)gridDim.x; b += K2_THREADS) s += a.cc_part[b];
-  const double cc = block_sum(s, red);
+  float sh = 0.f, sl = 0.f;
+  for (int b0 = tid; b0 < ncta; b0 += 4 * K2_THREADS) {
+    float2 v[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      v[q] = (b0 + q * K2_THREADS < ncta) ? __ldcg(a.cc_part + b0 + q * K2_THREADS) : make_float2(0.f, 0.f);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) ff_add(sh, sl, v[q].x, v[q].y);
+  }
+  const float2 ccf = ff_block_sum(sh, sl, redf);
   if (tid == 0) {
+    const double cc = (double)ccf.x + (double)ccf.y;
     *a.counter = 0u;
     Ctl* c = a.ctl;
     if (!isfinite(cc)) c->latched = 4;
     const double ccv = isfinite(cc) ? cc : 0.0;
-    const double ee = c->xx - ccv > 0.0 ? c->xx - ccv : 0.0;
+    const double ee = xx - ccv > 0.0 ? xx - ccv : 0.0;
     c->cc = ccv;
     c->ee = ee;
-    c->sum_xx += c->xx;
-    c->sum_ee += ee;
-    c->t += 1;
+    c->sum_xx = sum_xx + xx;
+    c->sum_ee = sum_ee + ee;
+    c->t = tcount + 1;
   }
   TTRACE(28);
 }

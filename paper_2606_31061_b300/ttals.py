@@ -204,8 +204,9 @@ class Stream:
         _check(load().ttals_profile(self._h, 1 if enable else 0), "ttals_profile")
 
     def profile_read(self):
-        """(ms level-1 solve, ms level-1 environment, ms whole update, pushes) since the last read."""
-        ms = (ctypes.c_double * 3)()
+        """(ms level-1 solve, ms level-1 factorisation, ms level-1 environment, ms whole update,
+        pushes) summed since the last read."""
+        ms = (ctypes.c_double * 4)()
         n = ctypes.c_int64()
         _check(load().ttals_profile_read(self._h, ms, ctypes.byref(n)), "ttals_profile_read")
-        return ms[0], ms[1], ms[2], n.value
+        return ms[0], ms[1], ms[2], ms[3], n.value
