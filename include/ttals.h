@@ -167,6 +167,31 @@ ttals_status ttals_stats_async(ttals_stream *s, double *out4, void *cuda_stream)
 ttals_status ttals_profile(ttals_stream *s, int enable);
 ttals_status ttals_profile_read(ttals_stream *s, double ms_out[4], int64_t *n_out);
 
+/*
+ * ttals_slice_error_noalloc - allocation-free slice error (the paper has no
+ *   counterpart: an evaluation helper around the per-slice error of Sec. 5.1).
+ *   Enqueues on cuda_stream the computation of out2_dev[0] = ||x||^2 and
+ *   out2_dev[1] = ||x - y||^2 (FP64 sums in a fixed order, deterministic) for two
+ *   device arrays of n elements, e.g. a slice x_t and the reconstruction written by
+ *   ttals_reconstruct.  x_dtype: F64, F32, F16 or BF16; y_dtype: F64 or F32.
+ *   out2_dev: 2 doubles of device memory, 8-byte aligned, owned by the caller.
+ * Allocates nothing: for callers that cannot allocate device memory at the point
+ *   of the call (a serving loop that checks accuracy between pushes on a stream it
+ *   must not stall, as cudaMalloc/cudaFree synchronise the device; a process whose
+ *   device memory is fully reserved by its own pool).  Its scratch is a static
+ *   device array of 64 KiB (+256 B) per device, which limits n to 2^26 = 67,108,864
+ *   elements.  The first call on each device resolves the scratch address with
+ *   that device current and should precede any stream capture on that device.
+ *   Each call first clears the scratch's ticket counter on cuda_stream.  Calls
+ *   that overlap in time on one device (different streams or host threads) share
+ *   that scratch and race: serialise them.
+ * Errors (nothing enqueued): EINVAL (NULL pointer, n < 1, n > 2^26 with a message in
+ *   ttals_last_error, unsupported dtype, misaligned pointer), ECUDA.
+ */
+ttals_status ttals_slice_error_noalloc(const void *x_dev, ttals_dtype x_dtype, const void *y_dev,
+                                       ttals_dtype y_dtype, int64_t n, double *out2_dev,
+                                       void *cuda_stream);
+
 /* Static text for a status code. */
 const char *ttals_status_string(ttals_status st);
 

@@ -28,6 +28,7 @@
 #include <cmath>
 #include <cstdint>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <type_traits>
 #include <vector>
@@ -873,6 +874,103 @@ ttals_status set_device(int dev) {
   return TTALS_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Allocation-free slice error: ||x||^2 and ||x - y||^2 of two device arrays.
+// For callers that cannot allocate device memory at the point of the call: a
+// serving loop that checks accuracy between pushes on a stream it must not stall
+// (cudaMalloc and cudaFree synchronise the device) or a process whose device memory
+// is fully reserved by its own pool.  Its scratch (per-CTA partial sums and a
+// completion ticket) is the static device array below, not memory of a stream.
+// ---------------------------------------------------------------------------
+constexpr int kErrThreads = 256;
+constexpr long long kErrPerCta = 16384;           // elements per CTA
+constexpr int kErrMaxCtas = 4096;                 // => at most 4096 * 16384 = 2^26 elements
+constexpr size_t kErrPartBytes = (size_t)kErrMaxCtas * 2 * sizeof(double);
+// [0, kErrPartBytes): partials (||x||^2, ||x-y||^2) per CTA; then the ticket counter,
+// which must be zero when a call starts (each call clears it on its stream first)
+static __device__ __align__(256) unsigned char g_err_scratch[kErrPartBytes + 256];
+
+// device address of g_err_scratch, resolved once per device with that device current
+constexpr int kErrMaxDevices = 64;
+void* g_err_scratch_addr[kErrMaxDevices] = {};
+std::mutex g_err_scratch_mu;
+
+ttals_status err_scratch_for_current_device(unsigned char** out) {
+  int dev = -1;
+  TT_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kErrMaxDevices) {
+    g_last_err = "ttals_slice_error_noalloc: device ordinal out of range";
+    return TTALS_EINVAL;
+  }
+  std::lock_guard<std::mutex> lk(g_err_scratch_mu);
+  if (!g_err_scratch_addr[dev]) {
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_err_scratch);
+    if (e != cudaSuccess || !p) {
+      g_last_err = std::string("cudaGetSymbolAddress(g_err_scratch): ") + cudaGetErrorString(e);
+      cudaGetLastError();
+      return TTALS_ECUDA;
+    }
+    g_err_scratch_addr[dev] = p;
+  }
+  *out = (unsigned char*)g_err_scratch_addr[dev];
+  return TTALS_OK;
+}
+
+// one CTA per kErrPerCta elements: FP64 sums in a fixed order, partials in the static
+// scratch, the last CTA (ticket) sums them in CTA order and resets the ticket
+template <typename TA, typename TB>
+__global__ void __launch_bounds__(kErrThreads) k_slice_error_noalloc(const TA* __restrict__ x,
+                                                                     const TB* __restrict__ y, long long n,
+                                                                     double* part, unsigned* ticket,
+                                                                     double* out) {
+  __shared__ double red[32];
+  __shared__ int last;
+  const long long b0 = (long long)blockIdx.x * kErrPerCta;
+  const long long b1 = (b0 + kErrPerCta < n) ? b0 + kErrPerCta : n;
+  double sx = 0.0, se = 0.0;
+  for (long long i = b0 + threadIdx.x; i < b1; i += kErrThreads) {
+    const double a = Cvt<TA>::d(x[i]), d = a - Cvt<TB>::d(y[i]);
+    sx = fma(a, a, sx);
+    se = fma(d, d, se);
+  }
+  sx = block_sum(sx, red);
+  se = block_sum(se, red);
+  if (threadIdx.x == 0) {
+    part[2 * blockIdx.x] = sx;
+    part[2 * blockIdx.x + 1] = se;
+    __threadfence();
+    last = (atomicAdd(ticket, 1u) == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  double tx = 0.0, te = 0.0;
+  for (int b = threadIdx.x; b < (int)gridDim.x; b += kErrThreads) {
+    tx += __ldcg(part + 2 * b);
+    te += __ldcg(part + 2 * b + 1);
+  }
+  tx = block_sum(tx, red);
+  te = block_sum(te, red);
+  if (threadIdx.x == 0) {
+    out[0] = tx;
+    out[1] = te;
+    *ticket = 0u;
+  }
+}
+
+template <typename TA>
+ttals_status launch_slice_error(const TA* x, const void* y, ttals_dtype yt, long long n, double* part,
+                                unsigned* ticket, double* out, cudaStream_t st) {
+  const unsigned grid = (unsigned)cdiv(n, kErrPerCta);
+  if (yt == TTALS_F64)
+    k_slice_error_noalloc<TA, double><<<grid, kErrThreads, 0, st>>>(x, (const double*)y, n, part, ticket, out);
+  else
+    k_slice_error_noalloc<TA, float><<<grid, kErrThreads, 0, st>>>(x, (const float*)y, n, part, ticket, out);
+  TT_CUDA(cudaGetLastError());
+  return TTALS_OK;
+}
+
 }  // namespace
 
 // ===========================================================================
@@ -1119,6 +1217,42 @@ ttals_status ttals_profile_read(ttals_stream* s, double ms_out[4], int64_t* n_ou
   *n_out = (int64_t)npush;
   s->ev_used = 0;
   return TTALS_OK;
+}
+
+ttals_status ttals_slice_error_noalloc(const void* x_dev, ttals_dtype x_dtype, const void* y_dev,
+                                       ttals_dtype y_dtype, int64_t n, double* out2_dev, void* cuda_stream) {
+  if (!x_dev || !y_dev || !out2_dev || n < 1) {
+    g_last_err = "ttals_slice_error_noalloc: NULL pointer or n < 1";
+    return TTALS_EINVAL;
+  }
+  if (n > (int64_t)kErrMaxCtas * kErrPerCta) {
+    g_last_err = "ttals_slice_error_noalloc: n = " + std::to_string((long long)n) +
+                 " exceeds the static scratch limit of " + std::to_string((long long)kErrMaxCtas * kErrPerCta) +
+                 " elements";
+    return TTALS_EINVAL;
+  }
+  if ((x_dtype < TTALS_F64 || x_dtype > TTALS_BF16) || (y_dtype != TTALS_F64 && y_dtype != TTALS_F32)) {
+    g_last_err = "ttals_slice_error_noalloc: unsupported dtype";
+    return TTALS_EINVAL;
+  }
+  const size_t xs = dtype_size(x_dtype), ys = dtype_size(y_dtype);
+  if (((uintptr_t)x_dev % xs) || ((uintptr_t)y_dev % ys) || ((uintptr_t)out2_dev % 8)) {
+    g_last_err = "ttals_slice_error_noalloc: misaligned pointer";
+    return TTALS_EINVAL;
+  }
+  unsigned char* scr = nullptr;
+  TT_TRY(err_scratch_for_current_device(&scr));
+  double* part = (double*)scr;
+  unsigned* ticket = (unsigned*)(scr + kErrPartBytes);
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  TT_CUDA(cudaMemsetAsync(ticket, 0, sizeof(unsigned), st));
+  switch (x_dtype) {
+    case TTALS_F64: return launch_slice_error((const double*)x_dev, y_dev, y_dtype, n, part, ticket, out2_dev, st);
+    case TTALS_F32: return launch_slice_error((const float*)x_dev, y_dev, y_dtype, n, part, ticket, out2_dev, st);
+    case TTALS_F16: return launch_slice_error((const __half*)x_dev, y_dev, y_dtype, n, part, ticket, out2_dev, st);
+    default:
+      return launch_slice_error((const __nv_bfloat16*)x_dev, y_dev, y_dtype, n, part, ticket, out2_dev, st);
+  }
 }
 
 }  // extern "C"

@@ -23,7 +23,8 @@ STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENONFINITE", 5: "ET
 EXPORTS = ("ttals_create", "ttals_destroy", "ttals_effective_ranks", "ttals_set_cores",
            "ttals_push_slice", "ttals_reconstruct", "ttals_cores", "ttals_stats", "ttals_step",
            "ttals_sync", "ttals_device_bytes", "ttals_status_string", "ttals_last_error",
-           "ttals_launch_count", "ttals_stats_async", "ttals_profile", "ttals_profile_read")
+           "ttals_launch_count", "ttals_stats_async", "ttals_profile", "ttals_profile_read",
+           "ttals_slice_error_noalloc")
 
 
 class TTALSError(RuntimeError):
@@ -68,6 +69,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "ttals_stats_async": (ctypes.c_int, [VP, VP, VP]),
         "ttals_profile": (ctypes.c_int, [VP, ctypes.c_int]),
         "ttals_profile_read": (ctypes.c_int, [VP, P(ctypes.c_double), I64P]),
+        "ttals_slice_error_noalloc": (ctypes.c_int, [VP, ctypes.c_int, VP, ctypes.c_int, ctypes.c_int64, VP, VP]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -210,3 +212,33 @@ class Stream:
         n = ctypes.c_int64()
         _check(load().ttals_profile_read(self._h, ms, ctypes.byref(n)), "ttals_profile_read")
         return ms[0], ms[1], ms[2], ms[3], n.value
+
+
+_TORCH_DTYPES = {"float64": "f64", "float32": "f32", "float16": "f16", "bfloat16": "bf16"}
+
+
+def slice_error_noalloc(x, y, out2, stream=None):
+    """ttals_slice_error_noalloc: enqueue out2[0] = ||x||^2, out2[1] = ||x - y||^2.
+
+    x, y: contiguous CUDA tensors of the same element count (y float64 or float32);
+    out2: a CUDA float64 tensor of 2 elements.  Allocates no device memory.
+    """
+    xt = DTYPES[_TORCH_DTYPES[str(x.dtype).replace("torch.", "")]]
+    yt = DTYPES[_TORCH_DTYPES[str(y.dtype).replace("torch.", "")]]
+    lib = load()
+    code = lib.ttals_slice_error_noalloc(ctypes.c_void_p(x.data_ptr()), xt, ctypes.c_void_p(y.data_ptr()), yt,
+                                         ctypes.c_int64(x.numel()), ctypes.c_void_p(out2.data_ptr()),
+                                         ctypes.c_void_p(_stream_handle(stream)))
+    if code != 0:
+        raise TTALSError(code, "ttals_slice_error_noalloc", lib.ttals_last_error().decode())
+
+
+def slice_error_noalloc_ptr(x_ptr: int, x_dtype: str, y_ptr: int, y_dtype: str, n: int, out2_ptr: int,
+                            stream=None):
+    """ttals_slice_error_noalloc on raw device pointers (see slice_error_noalloc)."""
+    lib = load()
+    code = lib.ttals_slice_error_noalloc(ctypes.c_void_p(x_ptr), DTYPES[x_dtype], ctypes.c_void_p(y_ptr),
+                                         DTYPES[y_dtype], ctypes.c_int64(n), ctypes.c_void_p(out2_ptr),
+                                         ctypes.c_void_p(_stream_handle(stream)))
+    if code != 0:
+        raise TTALSError(code, "ttals_slice_error_noalloc", lib.ttals_last_error().decode())
