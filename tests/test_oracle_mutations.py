@@ -41,7 +41,7 @@ PINS = [
     "test_closed_form_subspace_iteration_n3",
     "test_closed_form_saturated_n4",
     "test_exact_recovery_noiseless_tt_stream",
-    "test_monotonicity_prop31",
+    "test_monotonicity_prop41",
     "test_local_solve_is_bruteforce_least_squares",
     "test_temporal_row_is_bruteforce_lstsq",
 ]

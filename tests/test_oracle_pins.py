@@ -2,7 +2,7 @@
 
 Each test ties the oracle to something other than itself: a library routine
 (LAPACK QR / SVD / lstsq), a closed form derived from Algorithm 1, brute force
-on tiny inputs, or an inequality the paper proves (Prop. 3.1, Prop. 3.2).
+on tiny inputs, or an inequality the paper proves (Proposition 4.1 (Monotonicity), Proposition 4.2 (Temporal Smoothness Bound)).
 """
 import math
 
@@ -204,8 +204,8 @@ def test_orthogonality_invariants():
         assert st.log["right_orth_residual"] <= 1e-12
 
 
-def test_monotonicity_prop31():
-    """Prop. 3.1: f(G*) <= f(G_old) for every local solve.  A theorem for the lsq mode
+def test_monotonicity_prop41():
+    """Proposition 4.1 (Monotonicity): f(G*) <= f(G_old) for every local solve.  A theorem for the lsq mode
     (exact local least squares) and for the literal mode when r_{n-1} = 1 (then
     B_k B_k^T = I); with r_{n-1} > 1 the end-to-end bound E_t <= ||x_t - M_{t-1}|| holds."""
     for mode, ranks in (("lsq", (4, 5, 4, 3)), ("literal", (4, 5, 4, 1))):
@@ -229,8 +229,8 @@ def test_monotonicity_prop31():
         assert np.linalg.norm(x - xh) <= np.linalg.norm(x - st.log["prev_xhat"]) * (1 + 1e-12)
 
 
-def test_prop31_identity_under_orthogonality():
-    """Under A^T A = I, B B^T = I: f(G) = f(G*) + 1/2 ||G - G*||^2 (proof of Prop. 3.1)."""
+def test_prop41_identity_under_orthogonality():
+    """Under A^T A = I, B B^T = I: f(G) = f(G*) + 1/2 ||G - G*||^2 (proof of Proposition 4.1 (Monotonicity))."""
     dims = (4, 5, 3)
     r = O.clamp_ranks(dims, [3, 4, 1])
     cores, g = synth.init_cores(dims, r, seed=12)
@@ -247,8 +247,8 @@ def test_prop31_identity_under_orthogonality():
     assert abs(f - fs - 0.5 * np.sum((other - gt) ** 2)) <= 1e-10 * f
 
 
-def test_temporal_smoothness_prop32():
-    """Prop. 3.2: E_t <= E_{t-1} + ||x_t - x_{t-1}||."""
+def test_temporal_smoothness_prop42():
+    """Proposition 4.2 (Temporal Smoothness Bound): E_t <= E_{t-1} + ||x_t - x_{t-1}||."""
     sp, xs, r, cores, g = _stream("sensor", 25, dims=(6, 5, 4, 5), ranks=(4, 5, 4, 2), noise=0.02,
                                   change_every=9)
     xh, _ = O.run_stream(sp.dims, r, cores, g, xs)
