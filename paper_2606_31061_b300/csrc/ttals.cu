@@ -27,10 +27,12 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <string>
 #include <type_traits>
+#include <unordered_map>
 #include <vector>
 
 using namespace ttals;
@@ -161,6 +163,10 @@ struct ttals_stream {
   unsigned long long nlaunch = 0;      // kernels launched by this stream (host counter)
   // optional timing of the level-1 kernels: CUDA events recorded on the launch stream
   bool profiling = false;
+  // TTALS_NO_PDL=1 in the environment at creation: launch the fused kernels without
+  // programmatic dependent launch (each kernel then starts after its predecessor ends);
+  // used for profiler captures that replay one kernel of the chain
+  bool no_pdl = false;
   std::vector<cudaEvent_t> ev_pool;    // recorded events, in groups of kProfEvents per push
   size_t ev_used = 0;
   static constexpr int kProfEvents = 6; // push begin, solve1 begin, solve1 end, env1 begin, env1 end, push end
@@ -434,6 +440,24 @@ struct Impl final : ttals_stream {
     return TTALS_OK;
   }
 
+  // per-slice-address TMA maps {solve box, env box}; cleared when it reaches its cap
+  struct SliceMaps {
+    CUtensorMap m[2];
+  };
+  std::unordered_map<const void*, SliceMaps> map_cache;
+  const CUtensorMap* slice_maps(const TX* X) {
+    constexpr size_t kMapCacheCap = 1024;
+    auto it = map_cache.find((const void*)X);
+    if (it != map_cache.end()) return it->second.m;
+    if (map_cache.size() >= kMapCacheCap) map_cache.clear();
+    SliceMaps sm;
+    const bool bf = std::is_same<TX, __nv_bfloat16>::value;
+    if (!encode_map_2d(&sm.m[0], X, bf, dims[0], rest[1], fast::K1_BM) ||
+        !encode_map_2d(&sm.m[1], X, bf, dims[0], rest[1], k2_rch))
+      return nullptr;
+    return map_cache.emplace((const void*)X, sm).first->second.m;
+  }
+
   template <int NP>
   ttals_status launch_fast(const TX* X, cudaStream_t s) {
     if constexpr (kHalfIngest) {
@@ -445,15 +469,17 @@ struct Impl final : ttals_stream {
       at[0].val.clusterDim.y = (unsigned)k1_split;
       at[0].val.clusterDim.z = 1;
       at[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-      at[1].val.programmaticStreamSerializationAllowed = profiling ? 0 : 1;
-      // TMA maps of this slice (box 64 x 64 for the solve, 64 x rch for the env kernel)
-      const bool bf = std::is_same<TX, __nv_bfloat16>::value;
-      CUtensorMap mapX1, mapX2;
-      if (!encode_map_2d(&mapX1, X, bf, dims[0], rest[1], fast::K1_BM) ||
-          !encode_map_2d(&mapX2, X, bf, dims[0], rest[1], k2_rch)) {
+      at[1].val.programmaticStreamSerializationAllowed = (profiling || no_pdl) ? 0 : 1;
+      // TMA maps of this slice (box 64 x 64 for the solve, 64 x rch for the env kernel),
+      // cached by slice address: a stream fed from a ring of device buffers encodes each
+      // buffer's maps once
+      const CUtensorMap* maps = slice_maps(X);
+      if (!maps) {
         g_last_err = "cuTensorMapEncodeTiled failed";
         return TTALS_ECUDA;
       }
+      const CUtensorMap& mapX1 = maps[0];
+      const CUtensorMap& mapX2 = maps[1];
       // K1: local solve
       fast::SolveArgs a1{};
       a1.M = (int)dims[0];
@@ -1041,6 +1067,10 @@ ttals_status ttals_create(int n_slice_modes, const int64_t* dims, const int64_t*
     return TTALS_ECUDA;
   }
   ttals_stream* s = make_impl(c.ingest);
+  {
+    const char* e = std::getenv("TTALS_NO_PDL");
+    s->no_pdl = e && e[0] == '1';
+  }
   s->m = m;
   s->dims = d;
   s->full.assign(m + 1, 1);

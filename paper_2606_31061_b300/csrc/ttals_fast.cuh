@@ -338,6 +338,7 @@ __global__ void __launch_bounds__(K1_THREADS, 2)
 #pragma unroll
   for (int j = 0; j < NT; ++j) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.f;
   float ssh = 0.f, ssl = 0.f;    // ||x||^2 of the tiles seen by this thread (float-float)
+  int t_done = ntk;              // tiles consumed (fewer after a timed-out wait)
   for (int t = 0; t < ntk; ++t) {
     const int st = t % K1_STAGES;
     if (!mbar_wait(smem_u32(&bars[st]), (uint32_t)((t / K1_STAGES) & 1))) timeout_flag = 1;
@@ -369,6 +370,10 @@ __global__ void __launch_bounds__(K1_THREADS, 2)
     }
     two_sum_acc(ssh, ssl, ss);
     __syncthreads();          // every warp is done with stage st
+    if (timeout_flag) {       // uniform (read after the barrier): stop issuing, drain below
+      t_done = t + 1;
+      break;
+    }
     if (t == 0 && bzero && blockIdx.y == 0 && tid == 0)
       *reinterpret_cast<TX*>(smem + (stageB(0) - sbase)) = from_acc<TX>(0.f);
     if (tid == 0 && t + K1_STAGES < ntk) {
@@ -383,6 +388,13 @@ __global__ void __launch_bounds__(K1_THREADS, 2)
         tma_load_2d(stageB(st), &tmB, (int)(kbeg + (long long)tn * K1_BK), 0, bar);
       }
     }
+  }
+  if (t_done < ntk) {
+    // a wait gave up: wait (bounded) for the copies still in flight before the buffers are
+    // reused, then finish the cluster protocol with the step marked failed (ETIMEOUT)
+    for (int t = t_done; t < ntk && t < t_done + K1_STAGES - 1; ++t)
+      mbar_wait(smem_u32(&bars[t % K1_STAGES]), (uint32_t)((t / K1_STAGES) & 1));
+    __syncthreads();
   }
   if (tr0) TTRACE(1);
   TTRACE_CTA(2);
@@ -523,6 +535,7 @@ __global__ void __launch_bounds__(K1B_THREADS) k_fast_factor(FactorArgs a) {
   }
   cp_async_wait<0>();
   __syncthreads();
+  TTRACE(16);
   // ---- 1. Gram partial: thread (row group, 4 x 4 block); row groups summed in order
   if (tid < NRG * NBLK) {
     const int blk = tid % NBLK, rg = tid / NBLK, ib = blk / NB, jb = blk % NB;
@@ -552,6 +565,7 @@ __global__ void __launch_bounds__(K1B_THREADS) k_fast_factor(FactorArgs a) {
     for (int g = 0; g < NRG; ++g) sum += Gr[g * NP * NP + e];
     Wp[e] = sum;
   }
+  TTRACE(17);
   cluster_sync();
   {
     const uint32_t wb = smem_u32(Wp);
@@ -580,6 +594,7 @@ __global__ void __launch_bounds__(K1B_THREADS) k_fast_factor(FactorArgs a) {
   if (tid < 64) {
     const float d = tid < r ? W[tid * r + tid] : 0.f;
     dsc[tid] = d > 0.f ? rsqrtf(d) : 0.f;
+    invd[tid] = 0.f;
     if (tid < r && !(d > 0.f)) flags[1] = 1;
   }
   __syncthreads();
@@ -604,6 +619,7 @@ __global__ void __launch_bounds__(K1B_THREADS) k_fast_factor(FactorArgs a) {
 #pragma unroll
         for (int k = 0; k < 32; ++k) l[k] = 0.f;
         int ok = 1;
+        // left-looking, lane i holds row i of L; fully unrolled (register-indexed rows)
 #pragma unroll
         for (int j = 0; j < 32; ++j) {
           // W1 is symmetric: W[j][lane] = W[lane][j], read along the row (conflict-free)
@@ -618,10 +634,10 @@ __global__ void __launch_bounds__(K1B_THREADS) k_fast_factor(FactorArgs a) {
           }
           const float sv = (s0 + s1) + (s2 + s3);
           const float piv = __shfl_sync(0xffffffffu, sv, j);
-          if (!(piv > 1e-4f)) ok = 0;
+          if (j < r && !(piv > 1e-4f)) ok = 0;
           const float rl = rsqrtf(piv > 0.f ? piv : 1.f);
           l[j] = (lane == j) ? piv * rl : (lane > j ? sv * rl : 0.f);
-          if (lane == j) invd[j] = rl;
+          if (lane == j && j < r) invd[j] = rl;
         }
 #pragma unroll
         for (int k = 0; k < 32; ++k)
@@ -665,38 +681,69 @@ __global__ void __launch_bounds__(K1B_THREADS) k_fast_factor(FactorArgs a) {
     if (crank == 0) householder_cta<float, float>(a.Y, a.M, r, r, a.hh_work, a.Qfb, r, red);
     cluster_sync();                   // Qfb complete before the other ranks read it
   }
-  // ---- 3. Q1 rows: z = L^{-1} (D y) by forward substitution (Householder Q: z = q)
+  // ---- 3. Q1 rows: z = L^{-1} (D y) by forward substitution, in place in the row of Ys,
+  // in 8-column register blocks (Householder Q: z = q)
+  const int nb8 = (r + 7) / 8;
   for (int row = tid; row < nrows + 16; row += K1B_THREADS) {
-    float z[NP];
+    float* zr = Ys + row * LDY;
     if (row < myrows) {
       if (!fb) {
 #pragma unroll
         for (int c4 = 0; c4 < NP / 4; ++c4) {
-          const float4 y = *reinterpret_cast<const float4*>(Ys + row * LDY + 4 * c4);
-          z[4 * c4 + 0] = y.x * dsc[4 * c4 + 0];
-          z[4 * c4 + 1] = y.y * dsc[4 * c4 + 1];
-          z[4 * c4 + 2] = y.z * dsc[4 * c4 + 2];
-          z[4 * c4 + 3] = y.w * dsc[4 * c4 + 3];
+          float4 y = *reinterpret_cast<const float4*>(zr + 4 * c4);
+          y.x *= dsc[4 * c4];
+          y.y *= dsc[4 * c4 + 1];
+          y.z *= dsc[4 * c4 + 2];
+          y.w *= dsc[4 * c4 + 3];
+          *reinterpret_cast<float4*>(zr + 4 * c4) = y;
         }
+        for (int kb = 0; kb < nb8; ++kb) {
+          float zb[8];
+          {
+            const float4 u = *reinterpret_cast<const float4*>(zr + 8 * kb);
+            const float4 v = *reinterpret_cast<const float4*>(zr + 8 * kb + 4);
+            zb[0] = u.x; zb[1] = u.y; zb[2] = u.z; zb[3] = u.w;
+            zb[4] = v.x; zb[5] = v.y; zb[6] = v.z; zb[7] = v.w;
+          }
 #pragma unroll
-        for (int k = 0; k < NP; ++k) {
-          if (k < r) {
-            z[k] *= invd[k];
+          for (int k = 0; k < 8; ++k) {
+            zb[k] *= invd[8 * kb + k];                 // zero past r
 #pragma unroll
-            for (int i4 = (k + 1) / 4; i4 < NP / 4; ++i4) {
-              const float4 lv = *reinterpret_cast<const float4*>(LT + k * LDT + 4 * i4);
-              if (4 * i4 + 0 > k) z[4 * i4 + 0] = fmaf(-lv.x, z[k], z[4 * i4 + 0]);
-              if (4 * i4 + 1 > k) z[4 * i4 + 1] = fmaf(-lv.y, z[k], z[4 * i4 + 1]);
-              if (4 * i4 + 2 > k) z[4 * i4 + 2] = fmaf(-lv.z, z[k], z[4 * i4 + 2]);
-              if (4 * i4 + 3 > k) z[4 * i4 + 3] = fmaf(-lv.w, z[k], z[4 * i4 + 3]);
+            for (int i = k + 1; i < 8; ++i) zb[i] = fmaf(-LT[(8 * kb + k) * LDT + 8 * kb + i], zb[k], zb[i]);
+          }
+          *reinterpret_cast<float4*>(zr + 8 * kb) = make_float4(zb[0], zb[1], zb[2], zb[3]);
+          *reinterpret_cast<float4*>(zr + 8 * kb + 4) = make_float4(zb[4], zb[5], zb[6], zb[7]);
+          for (int jb = kb + 1; jb < nb8; ++jb) {
+            const float4 u = *reinterpret_cast<const float4*>(zr + 8 * jb);
+            const float4 v = *reinterpret_cast<const float4*>(zr + 8 * jb + 4);
+            float zj[8] = {u.x, u.y, u.z, u.w, v.x, v.y, v.z, v.w};
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+              const float4 la = *reinterpret_cast<const float4*>(LT + (8 * kb + k) * LDT + 8 * jb);
+              const float4 lb = *reinterpret_cast<const float4*>(LT + (8 * kb + k) * LDT + 8 * jb + 4);
+              zj[0] = fmaf(-la.x, zb[k], zj[0]);
+              zj[1] = fmaf(-la.y, zb[k], zj[1]);
+              zj[2] = fmaf(-la.z, zb[k], zj[2]);
+              zj[3] = fmaf(-la.w, zb[k], zj[3]);
+              zj[4] = fmaf(-lb.x, zb[k], zj[4]);
+              zj[5] = fmaf(-lb.y, zb[k], zj[5]);
+              zj[6] = fmaf(-lb.z, zb[k], zj[6]);
+              zj[7] = fmaf(-lb.w, zb[k], zj[7]);
             }
-          } else {
-            z[k] = 0.f;
+            *reinterpret_cast<float4*>(zr + 8 * jb) = make_float4(zj[0], zj[1], zj[2], zj[3]);
+            *reinterpret_cast<float4*>(zr + 8 * jb + 4) = make_float4(zj[4], zj[5], zj[6], zj[7]);
           }
         }
       } else {
+        for (int c = 0; c < NP; ++c) zr[c] = c < r ? a.Qfb[(long long)(row0 + row) * r + c] : 0.f;
+      }
+    }
+    float z[NP];
+    if (row < myrows) {
 #pragma unroll
-        for (int c = 0; c < NP; ++c) z[c] = c < r ? a.Qfb[(long long)(row0 + row) * r + c] : 0.f;
+      for (int c4 = 0; c4 < NP / 4; ++c4) {
+        const float4 v = *reinterpret_cast<const float4*>(zr + 4 * c4);
+        z[4 * c4] = v.x; z[4 * c4 + 1] = v.y; z[4 * c4 + 2] = v.z; z[4 * c4 + 3] = v.w;
       }
     } else {
 #pragma unroll
@@ -714,6 +761,7 @@ __global__ void __launch_bounds__(K1B_THREADS) k_fast_factor(FactorArgs a) {
       *reinterpret_cast<uint4*>(Qs + row * LQ + 8 * c8) = make_uint4(w[0], w[1], w[2], w[3]);
     }
   }
+  TTRACE(18);
   __syncthreads();
   // my rows of Q1, coalesced: ingest-type copy (16-byte chunks) and FP32 state
   for (int e = tid; e < myrows * (NP / 8); e += K1B_THREADS) {
@@ -747,6 +795,7 @@ __global__ void __launch_bounds__(K1B_THREADS) k_fast_factor(FactorArgs a) {
       Wp[(row + 8) * NP + col + 1] = acc[3];
     }
   }
+  TTRACE(19);
   cluster_sync();
   // W2 = the ranks' partials in rank order (every rank)
   {
