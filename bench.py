@@ -166,7 +166,6 @@ def time_arm(ingest, steps, warmup, pool, dist_on, sampler_idx):
         import torch.distributed as dist
         dist.barrier()
     torch.cuda.synchronize()
-    n0 = st.launch_count
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     clocks = None
@@ -185,6 +184,7 @@ def time_arm(ingest, steps, warmup, pool, dist_on, sampler_idx):
         st.push_ptr(p, h)
     host_us = (time.perf_counter() - h0) / nb * 1e6
     torch.cuda.synchronize()
+    n0 = st.launch_count
     w0 = time.time()
     e0.record(stream)
     for p in order:
@@ -406,8 +406,10 @@ def main():
             "warmup": args.warmup, "ms_per_step": r["ms"] / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": args.ingest, "data": "synthetic",
             "config": {"workload": WORKLOAD, "ingest": args.ingest,
-                       "precision": f"{args.ingest.upper()} ingest, FP32 accumulation and state, "
-                                    "FP32 Cholesky factor + FP64 polar re-orthogonalisation",
+                       "precision": (f"{args.ingest.upper()} ingest, FP32 accumulation and state; basis from an "
+                                     "FP32 scaled Cholesky with an exact projector correction for the rounded "
+                                     "basis; FP64 r x r factor when cores are exported") if args.ingest != "f32" else
+                                    "FP32 ingest and state; Cholesky-QR (FP32 factor, FP64 sums) + FP64 polar pass",
                        "l2": f"inputs larger than L2: {args.pool}-frame pool "
                              f"({args.pool * slice_bytes / 1e6:.0f} MB), played forward and backward",
                        "parallelism": f"replicas x{world}" if world > 1 else "single stream"},

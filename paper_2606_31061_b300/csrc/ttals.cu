@@ -1201,7 +1201,7 @@ int ttals_debug_trace(unsigned long long* out, int n) {
   return cudaMemcpyFromSymbol(out, ttals::g_ttals_trace, (size_t)n * 8) == cudaSuccess ? 0 : 3;
 }
 int ttals_debug_trace_cta(unsigned long long* out, int n) {
-  if (n > 2048) n = 2048;
+  if (n > 4096) n = 4096;
   return cudaMemcpyFromSymbol(out, ttals::g_ttals_cta, (size_t)n * 8) == cudaSuccess ? 0 : 3;
 }
 #endif

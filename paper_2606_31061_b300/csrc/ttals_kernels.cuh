@@ -27,23 +27,29 @@ __device__ unsigned long long g_ttals_trace[128];
       ::ttals::g_ttals_trace[(i)] = t_;                                            \
     }                                                                              \
   } while (0)
-// TTRACE_CTA(k): per-CTA timestamps (slot k < 4) of up to 512 CTAs of a traced kernel
-__device__ unsigned long long g_ttals_cta[512 * 4];
-#define TTRACE_CTA(k)                                                              \
+// TTRACE_CTA(k) / TTRACE_CTA2(k): per-CTA timestamps (slot k < 4) of up to 512 CTAs of
+// two traced kernels (first and second half of the array)
+__device__ unsigned long long g_ttals_cta[1024 * 4];
+#define TTRACE_CTA_AT(base, k)                                                     \
   do {                                                                             \
     const unsigned b_ = blockIdx.y * gridDim.x + blockIdx.x;                       \
     if (threadIdx.x == 0 && b_ < 512) {                                            \
       unsigned long long t_;                                                       \
       asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t_));                       \
-      ::ttals::g_ttals_cta[b_ * 4 + (k)] = t_;                                     \
+      ::ttals::g_ttals_cta[((base) + b_) * 4 + (k)] = t_;                          \
     }                                                                              \
   } while (0)
+#define TTRACE_CTA(k) TTRACE_CTA_AT(0, k)
+#define TTRACE_CTA2(k) TTRACE_CTA_AT(512, k)
 #else
 #define TTRACE(i) \
   do {            \
   } while (0)
 #define TTRACE_CTA(k) \
   do {                \
+  } while (0)
+#define TTRACE_CTA2(k) \
+  do {                 \
   } while (0)
 #endif
 
