@@ -178,9 +178,10 @@ def time_arm(ingest, steps, warmup, pool, dist_on, sampler_idx):
     # host cost of one push: a short burst enqueued while the device is busy (the launch
     # queue does not fill, so no back-pressure is included)
     torch.cuda._sleep(int(2e8))
-    nb = min(64, steps)
+    nb = min(64, warmup)
+    burst = [ptrs[pingpong(t, P)] for t in range(nb)]   # slices seen in the warm-up (maps cached)
     h0 = time.perf_counter()
-    for p in order[:nb]:
+    for p in burst:
         st.push_ptr(p, h)
     host_us = (time.perf_counter() - h0) / nb * 1e6
     torch.cuda.synchronize()

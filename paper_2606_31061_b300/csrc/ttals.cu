@@ -284,6 +284,7 @@ struct Impl final : ttals_stream {
   float* fNx = nullptr;         // W2^{-1} - I (r x r)
   float* fQfb = nullptr;
   float2* fCC = nullptr;       // float-float partials of ||x^||^2 (env CTAs)
+  bool k2_single = false;       // environment kernel: one CTA per 64-column tile over all rows
   unsigned* fCounter = nullptr; // [2]
   CUtensorMap mapB[2];          // TMA maps of fCh[p] (r x rest_1, box 64 x NP)
 
@@ -354,8 +355,12 @@ struct Impl final : ttals_stream {
     if constexpr (kHalfIngest) {
       TT_CUDA(cudaFuncSetAttribute(fast::k_fast_solve<TX, NP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    (int)k1_smem));
-      TT_CUDA(cudaFuncSetAttribute(fast::k_fast_env<TX, NP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   (int)k2_smem));
+      if (k2_single)
+        TT_CUDA(cudaFuncSetAttribute(fast::k_fast_env1<TX, NP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)k2_smem));
+      else
+        TT_CUDA(cudaFuncSetAttribute(fast::k_fast_env<TX, NP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)k2_smem));
       TT_CUDA(cudaFuncSetAttribute(fast::k_fast_factor<TX, NP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    (int)fast::k1b_smem_bytes((int)dims[0], rk(1), NP)));
     }
@@ -400,6 +405,23 @@ struct Impl final : ttals_stream {
     if (k2_nq == 0) k2_nq = 8;
     k2_rch = (int)(cdiv(cdiv(M, k2_nq), 16) * 16);
     k2_smem = k2_bytes(k2_rch);
+    {
+      bool fits = false;
+      size_t b1 = 0;
+      switch (np_) {
+        case 16: fits = fast::k2s_fits<16>((int)M, r); b1 = fast::k2s_smem_bytes<16>((int)M, r); break;
+        case 32: fits = fast::k2s_fits<32>((int)M, r); b1 = fast::k2s_smem_bytes<32>((int)M, r); break;
+        case 64: fits = fast::k2s_fits<64>((int)M, r); b1 = fast::k2s_smem_bytes<64>((int)M, r); break;
+        default: break;
+      }
+      if (fits && std::getenv("TTALS_ENV_CLUSTER") == nullptr) {
+        k2_single = true;
+        k2_nq = 1;
+        k2_cols = (int)cdiv(J, fast::K2S_BN);
+        k2_rch = fast::k2s_box_rows((int)M);      // TMA box height of the env kernel's X map
+        k2_smem = b1;
+      }
+    }
     switch (np_) {
       case 16: k1_smem = fast::k1_smem_bytes<16>(); break;
       case 32: k1_smem = fast::k1_smem_bytes<32>(); break;
@@ -408,7 +430,7 @@ struct Impl final : ttals_stream {
     }
     // after the main loop the solve CTA reuses its buffers: P (64 x NP), Gram (r x r), rows
     k1_smem = std::max(k1_smem, (size_t)(64 * np_ + r * r + 64 * r) * 4 + 64);
-    if (k2_smem > 220 * 1024 || k2_rch > 256) return TTALS_OK;
+    if (k2_smem > 226 * 1024 || k2_rch > 256) return TTALS_OK;
     if (!tensor_map_encoder()) return TTALS_OK;
     switch (np_) {
       case 16: TT_TRY(set_fast_attrs<16>()); break;
@@ -556,9 +578,15 @@ struct Impl final : ttals_stream {
       c2.blockDim = dim3(fast::K2_THREADS, 1, 1);
       c2.dynamicSmemBytes = k2_smem;
       c2.stream = s;
-      c2.attrs = at;
-      c2.numAttrs = 2;
-      TT_CUDA(cudaLaunchKernelEx(&c2, fast::k_fast_env<TX, NP>, mapX2, a2));
+      if (k2_single) {
+        c2.attrs = at + 1;       // no cluster
+        c2.numAttrs = 1;
+        TT_CUDA(cudaLaunchKernelEx(&c2, fast::k_fast_env1<TX, NP>, mapX2, a2));
+      } else {
+        c2.attrs = at;
+        c2.numAttrs = 2;
+        TT_CUDA(cudaLaunchKernelEx(&c2, fast::k_fast_env<TX, NP>, mapX2, a2));
+      }
       ++nlaunch;
       TT_TRY(mark(4, s));
       finalized[np] = false;

@@ -214,11 +214,19 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t
                : "memory");
 }
 
-// sum of n (<= 8) values loaded from distributed shared memory, loads issued together
+// the float at local address `a` in cluster rank q, or 0 for q >= n: the load always targets
+// a valid rank (q clamped to n-1) and the value is masked, so no remote access depends on the
+// guard being compiled as a branch
+__device__ __forceinline__ float dsmem_ld_rank(uint32_t a, int q, int n) {
+  const float v = dsmem_ld_f32(dsmem_addr(a, (uint32_t)(q < n ? q : n - 1)));
+  return q < n ? v : 0.f;
+}
+
+// sum of n (1..8) values loaded from distributed shared memory, loads issued together
 __device__ __forceinline__ float dsmem_sum8(uint32_t local_addr, int n) {
   float v[8];
 #pragma unroll
-  for (int q = 0; q < 8; ++q) v[q] = (q < n) ? dsmem_ld_f32(dsmem_addr(local_addr, q)) : 0.f;
+  for (int q = 0; q < 8; ++q) v[q] = dsmem_ld_rank(local_addr, q, n);
   float s = 0.f;
 #pragma unroll
   for (int q = 0; q < 8; ++q) s += v[q];
@@ -475,7 +483,7 @@ __host__ __device__ constexpr size_t k1b_smem_bytes(int M, int r, int np) {
 }
 
 template <typename TX, int NP>
-__global__ void __launch_bounds__(K1B_THREADS) k_fast_factor(FactorArgs a) {
+__global__ void __launch_bounds__(K1B_THREADS, 1) k_fast_factor(FactorArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   constexpr int LDY = NP + 4, LQ = NP + 8, LDT = NP + 4;
   constexpr int NB = NP / 4, NBLK = NB * NB, NRG = k1b_rgroups(NP);
@@ -574,9 +582,13 @@ __global__ void __launch_bounds__(K1B_THREADS) k_fast_factor(FactorArgs a) {
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
         const int e = e0 + u * K1B_THREADS;
-        const uint32_t la = wb + (uint32_t)((e / r) * NP + e % r) * 4u;
+        const int ec = e < rr ? e : rr - 1;            // in-range address; value masked below
+        const uint32_t la = wb + (uint32_t)((ec / r) * NP + ec % r) * 4u;
 #pragma unroll
-        for (int q = 0; q < KB_CLUSTER; ++q) v[u][q] = e < rr ? dsmem_ld_f32(dsmem_addr(la, (uint32_t)q)) : 0.f;
+        for (int q = 0; q < KB_CLUSTER; ++q) {
+          const float x = dsmem_ld_rank(la, q, KB_CLUSTER);
+          v[u][q] = e < rr ? x : 0.f;
+        }
       }
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
@@ -805,9 +817,13 @@ __global__ void __launch_bounds__(K1B_THREADS) k_fast_factor(FactorArgs a) {
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
         const int e = e0 + u * K1B_THREADS;
-        const uint32_t la = wb + (uint32_t)((e / r) * NP + e % r) * 4u;
+        const int ec = e < rr ? e : rr - 1;            // in-range address; value masked below
+        const uint32_t la = wb + (uint32_t)((ec / r) * NP + ec % r) * 4u;
 #pragma unroll
-        for (int q = 0; q < KB_CLUSTER; ++q) v[u][q] = e < rr ? dsmem_ld_f32(dsmem_addr(la, (uint32_t)q)) : 0.f;
+        for (int q = 0; q < KB_CLUSTER; ++q) {
+          const float x = dsmem_ld_rank(la, q, KB_CLUSTER);
+          v[u][q] = e < rr ? x : 0.f;
+        }
       }
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
@@ -829,16 +845,31 @@ __global__ void __launch_bounds__(K1B_THREADS) k_fast_factor(FactorArgs a) {
     float* U = Gr;                   // nr x r
     for (int e = tid; e < nr * r; e += K1B_THREADS) {
       const int i = i0 + e / r, j = e % r;
-      float sum = 0.f;
-      for (int k = 0; k < r; ++k)
-        sum = fmaf(W[i * r + k] - (i == k ? 1.f : 0.f), W[k * r + j] - (k == j ? 1.f : 0.f), sum);
-      U[e] = sum;
+      float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+      int k = 0;
+      for (; k + 3 < r; k += 4) {
+        s0 = fmaf(W[i * r + k] - (i == k ? 1.f : 0.f), W[k * r + j] - (k == j ? 1.f : 0.f), s0);
+        s1 = fmaf(W[i * r + k + 1] - (i == k + 1 ? 1.f : 0.f), W[(k + 1) * r + j] - (k + 1 == j ? 1.f : 0.f), s1);
+        s2 = fmaf(W[i * r + k + 2] - (i == k + 2 ? 1.f : 0.f), W[(k + 2) * r + j] - (k + 2 == j ? 1.f : 0.f), s2);
+        s3 = fmaf(W[i * r + k + 3] - (i == k + 3 ? 1.f : 0.f), W[(k + 3) * r + j] - (k + 3 == j ? 1.f : 0.f), s3);
+      }
+      for (; k < r; ++k) s0 = fmaf(W[i * r + k] - (i == k ? 1.f : 0.f), W[k * r + j] - (k == j ? 1.f : 0.f), s0);
+      U[e] = (s0 + s1) + (s2 + s3);
     }
     __syncthreads();
     for (int e = tid; e < nr * r; e += K1B_THREADS) {
       const int i = i0 + e / r, j = e % r;
-      float v = 0.f;
-      for (int k = 0; k < r; ++k) v = fmaf(U[(e / r) * r + k], W[k * r + j] - (k == j ? 1.f : 0.f), v);
+      const float* ur = U + (e / r) * r;
+      float v0 = 0.f, v1 = 0.f, v2 = 0.f, v3 = 0.f;
+      int k = 0;
+      for (; k + 3 < r; k += 4) {
+        v0 = fmaf(ur[k], W[k * r + j] - (k == j ? 1.f : 0.f), v0);
+        v1 = fmaf(ur[k + 1], W[(k + 1) * r + j] - (k + 1 == j ? 1.f : 0.f), v1);
+        v2 = fmaf(ur[k + 2], W[(k + 2) * r + j] - (k + 2 == j ? 1.f : 0.f), v2);
+        v3 = fmaf(ur[k + 3], W[(k + 3) * r + j] - (k + 3 == j ? 1.f : 0.f), v3);
+      }
+      for (; k < r; ++k) v0 = fmaf(ur[k], W[k * r + j] - (k == j ? 1.f : 0.f), v0);
+      const float v = (v0 + v1) + (v2 + v3);
       const float d2 = W[i * r + j] - (i == j ? 1.f : 0.f);
       a.Nx[i * r + j] = -d2 + U[e] - v;
       a.W2st[i * r + j] = W[i * r + j];
@@ -847,6 +878,43 @@ __global__ void __launch_bounds__(K1B_THREADS) k_fast_factor(FactorArgs a) {
   }
   cluster_wait();
   TTRACE(15);
+}
+
+// ||x^||^2 terms f_c (f + Nx f)_c of the columns of an F tile held as sF[jl*ldf + c] (c < r),
+// and the state writes of those columns.  Thread t owns column jl = t % 64 (+64, ...) and
+// the NP/4 rows c of group t / 64 (256 threads); Nx is NP x NP with zeros past r.  Adds to
+// the thread's float-float partial (ph, pl).
+template <typename TX, int NP>
+__device__ __forceinline__ void env_columns_out(const float* sF, int ldf, const float* sN, int ncols, int r,
+                                                long long J, long long gj0, float* Cst, TX* Chst, float scale,
+                                                float& ph, float& pl) {
+  const int cg = threadIdx.x / 64;
+  for (int jl = threadIdx.x % 64; jl < ncols; jl += 64) {
+    float fv[NP];
+#pragma unroll
+    for (int b = 0; b < NP; ++b) fv[b] = b < r ? sF[jl * ldf + (b < r ? b : 0)] : 0.f;
+    const long long gj = gj0 + jl;
+#pragma unroll
+    for (int q = 0; q < NP / 4; ++q) {
+      const int c = cg * (NP / 4) + q;
+      if (c < r) {
+        const float* nrow = sN + c * NP;
+        float g0 = 0.f, g1 = 0.f, g2 = 0.f, g3 = 0.f;
+#pragma unroll
+        for (int b4 = 0; b4 < NP / 4; ++b4) {
+          const float4 nv = *reinterpret_cast<const float4*>(nrow + 4 * b4);
+          g0 = fmaf(nv.x, fv[4 * b4], g0);
+          g1 = fmaf(nv.y, fv[4 * b4 + 1], g1);
+          g2 = fmaf(nv.z, fv[4 * b4 + 2], g2);
+          g3 = fmaf(nv.w, fv[4 * b4 + 3], g3);
+        }
+        const float fc = sF[jl * ldf + c];
+        two_sum_acc(ph, pl, fc * (fc + ((g0 + g1) + (g2 + g3))));
+        Cst[(long long)c * J + gj] = fc;
+        Chst[(long long)c * J + gj] = from_acc<TX>(fc * scale);
+      }
+    }
+  }
 }
 
 // ================================================================ K2: environment
@@ -882,9 +950,9 @@ struct EnvArgs {
 
 template <int NP>
 constexpr size_t k2_smem_bytes(int rch, int r) {
-  // X block (2 x rch x 128 B) | Q1 tile | partial tile P (BN x (NP+8)) | my columns F | Nx
+  // X block (2 x rch x 128 B) | Q1 tile | partial tile P (BN x (NP+8)) | my columns F | Nx (NP x NP)
   return 1024 + (size_t)rch * 256 + (size_t)rch * (NP + 8) * 2 + (size_t)K2_BN * (NP + 8) * 4 +
-         (size_t)K2_BN * (r + 1) * 4 + (size_t)r * r * 4 + 64;
+         (size_t)K2_BN * (r + 1) * 4 + (size_t)NP * NP * 4 + 64;
 }
 
 template <typename TX, int NP>
@@ -962,8 +1030,10 @@ __global__ void __launch_bounds__(K2_THREADS, 2)
       const bool ok = gi < a.M;
       cp_async16(smem_u32(sQ + row * (NP + 8) + ch * 8), Qh + (ok ? (long long)gi * NP + ch * 8 : 0), ok ? 16u : 0u);
     }
-    for (int e = tid; e < rr; e += K2_THREADS) cp_async4(smem_u32(sN + e), a.Nx + e);
+    for (int e = tid; e < rr; e += K2_THREADS) cp_async4(smem_u32(sN + (e / r) * NP + e % r), a.Nx + e);
     cp_async_commit();
+    for (int e = tid; e < NP * NP; e += K2_THREADS)
+      if (e / NP >= r || e % NP >= r) sN[e] = 0.f;
     cp_async_wait<0>();
   }
   if (!mbar_wait(smem_u32(&xbar), 0)) timeout_flag = 1;
@@ -1020,10 +1090,14 @@ __global__ void __launch_bounds__(K2_THREADS, 2)
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
         const int e = e0 + u * K2_THREADS;
-        const int jl = e / r, c = e % r;
+        const int ec = e < nmy * r ? e : nmy * r - 1;  // in-range address; value masked below
+        const int jl = ec / r, c = ec % r;
         const uint32_t la = Pb + (uint32_t)((jb + jl) * LDP + c) * 4u;
 #pragma unroll
-        for (int q = 0; q < 8; ++q) v[u][q] = (e < nmy * r && q < nq) ? dsmem_ld_f32(dsmem_addr(la, q)) : 0.f;
+        for (int q = 0; q < 8; ++q) {
+          const float x = dsmem_ld_rank(la, q, nq);
+          v[u][q] = e < nmy * r ? x : 0.f;
+        }
       }
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
@@ -1048,17 +1122,7 @@ __global__ void __launch_bounds__(K2_THREADS, 2)
   if (ct == 0 && crank == 0 && tid == 0) *a.ch_shift = shift;
   const float scale = ldexpf(1.0f, -shift);
   float ph = 0.f, pl = 0.f;     // float-float partial of ||x^||^2
-  for (int e = tid; e < nmy * r; e += K2_THREADS) {
-    const int c = e / nmy, jl = e % nmy;
-    const long long gj = j0 + jb + jl;
-    const float f = sF[jl * LDF + c];
-    a.Cst[(long long)c * a.J + gj] = f;
-    ((TX*)a.Chst)[(long long)c * a.J + gj] = from_acc<TX>(f * scale);
-    // f_c * (f + Nx f)_c
-    float g = f;
-    for (int b = 0; b < r; ++b) g = fmaf(sN[c * r + b], sF[jl * LDF + b], g);
-    two_sum_acc(ph, pl, f * g);
-  }
+  env_columns_out<TX, NP>(sF, LDF, sN, nmy, r, a.J, j0 + jb, a.Cst, (TX*)a.Chst, scale, ph, pl);
   const float2 cc_cta = ff_block_sum(ph, pl, redf);
   if (tr0) TTRACE(26);
   // one partial per CTA; the last CTA of the grid sums them in a fixed order
@@ -1081,6 +1145,226 @@ __global__ void __launch_bounds__(K2_THREADS, 2)
       v[q] = (b0 + q * K2_THREADS < ncta) ? __ldcg(a.cc_part + b0 + q * K2_THREADS) : make_float2(0.f, 0.f);
 #pragma unroll
     for (int q = 0; q < 4; ++q) ff_add(sh, sl, v[q].x, v[q].y);
+  }
+  const float2 ccf = ff_block_sum(sh, sl, redf);
+  if (tid == 0) {
+    const double cc = (double)ccf.x + (double)ccf.y;
+    *a.counter = 0u;
+    Ctl* c = a.ctl;
+    if (!isfinite(cc)) c->latched = 4;
+    const double ccv = isfinite(cc) ? cc : 0.0;
+    const double ee = xx - ccv > 0.0 ? xx - ccv : 0.0;
+    c->cc = ccv;
+    c->ee = ee;
+    c->sum_xx = sum_xx + xx;
+    c->sum_ee = sum_ee + ee;
+    c->t = tcount + 1;
+  }
+  TTRACE(28);
+}
+
+// ================================================================ K2 (single-CTA tiles)
+// F^T = X_(1)^T Q1 for a 64-column tile of X over all I_1 rows in one CTA (no cluster, no
+// split over rows): the tile's X block (I_1 x 128 B, 128B-swizzled TMA boxes of RB rows) is
+// requested before the dependency wait and arrives while the factor kernel runs; Q1 (ingest
+// type, I_1 x NP) comes from L2 into an XOR-swizzled layout (conflict-free ldmatrix).  The 8
+// warps split the rows and their partial tiles are summed in shared memory in warp order.
+// Used when the X block and Q1 fit in one CTA's shared memory.
+constexpr int K2S_BN = 64;            // slice columns j per CTA
+
+// byte offset of 16-byte chunk c of row `row` of the NP-wide Q1 tile
+template <int NP>
+__device__ __forceinline__ uint32_t qswz(int row, int c) {
+  constexpr int CPR = NP / 8;         // chunks per row
+  constexpr int G = 8 / CPR;          // rows per 128 bytes
+  return (uint32_t)(row * NP * 2 + ((c ^ ((row / G) & (CPR - 1))) << 4));
+}
+
+// rows of X per TMA box and boxes per tile (rows padded to a multiple of 16 for the k-steps)
+__host__ __device__ constexpr int k2s_box_rows(int M) {
+  return (((M + ((M + 255) / 256) - 1) / ((M + 255) / 256)) + 15) / 16 * 16;
+}
+__host__ __device__ constexpr int k2s_boxes(int M) { return (M + 255) / 256; }
+template <int NP>
+__host__ __device__ constexpr size_t k2s_smem_bytes(int M, int r) {
+  return 1024 + (size_t)k2s_boxes(M) * k2s_box_rows(M) * 128 + (size_t)((M + 15) / 16 * 16) * NP * 2 +
+         (size_t)NP * NP * 4 + 64 + 0 * r;
+}
+// the warp partials (8 x 64 x (NP+8)) and my columns of F (64 x (r+1)) reuse the X block
+template <int NP>
+__host__ __device__ constexpr bool k2s_fits(int M, int r) {
+  return NP != 48 && k2s_smem_bytes<NP>(M, r) <= 225 * 1024 &&
+         (size_t)8 * K2S_BN * (NP + 8) * 4 + (size_t)K2S_BN * (r + 1) * 4 <=
+             (size_t)k2s_boxes(M) * k2s_box_rows(M) * 128;
+}
+
+template <typename TX, int NP>
+__global__ void __launch_bounds__(K2_THREADS, 1)
+    k_fast_env1(const __grid_constant__ CUtensorMap tmX, EnvArgs a) {
+  constexpr int NT = NP / 8;          // n8-tiles of the output per warp
+  constexpr int MT = K2S_BN / 16;     // m16-tiles (64 columns)
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+  const int M = a.M, r = a.r, rr = r * r;
+  const int RB = k2s_box_rows(M), NBX = k2s_boxes(M);
+  const int Mp = (M + 15) / 16 * 16;
+  const uint32_t xs = smem_u32(smem);                                  // X block, row i at i*128
+  unsigned char* qbase = smem + (size_t)NBX * RB * 128;               // Q1, swizzled
+  const uint32_t qs = smem_u32(qbase);
+  float* sN = reinterpret_cast<float*>(qbase + (size_t)Mp * NP * 2);  // Nx, NP x NP, zero past r
+  constexpr int LDR = NP + 8;                                          // float2 stores: 2 wavefronts
+  float* RED = reinterpret_cast<float*>(smem);                        // [8][64][NP+8] after the product
+  const int LDF = r + 1;
+  float* sF = RED + 8 * K2S_BN * LDR;                                  // [64][r+1]
+  __shared__ __align__(8) uint64_t xbar;
+  __shared__ float redf[64];
+  __shared__ int last_flag;
+  __shared__ int timeout_flag;
+
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int ct = blockIdx.x;
+  const long long j0 = (long long)ct * K2S_BN;
+  const int xcols = (a.J - j0 < K2S_BN) ? (int)(a.J - j0) : K2S_BN;
+  const bool tr0 = (blockIdx.x == 0);
+
+  // 1. this CTA's X block through the TMA engine (independent of the previous kernels)
+  if (tid == 0) {
+    asm volatile("prefetch.tensormap [%0];\n" ::"l"(reinterpret_cast<uint64_t>(&tmX)) : "memory");
+    mbar_init(smem_u32(&xbar), 1);
+    mbar_fence_init();
+    timeout_flag = 0;
+    const uint32_t bar = smem_u32(&xbar);
+    mbar_arrive_expect_tx(bar, (uint32_t)NBX * RB * 128);
+    for (int b = 0; b < NBX; ++b) tma_load_2d(xs + (uint32_t)b * RB * 128, &tmX, (int)j0, b * RB, bar);
+  }
+  if (tr0) TTRACE(20);
+  // 2. wait for the factor kernel (Q1, Nx, ctl)
+  pdl_wait();
+  pdl_trigger();
+  if (tr0) TTRACE(21);
+  const double xx = a.ctl->xx;     // ||x||^2 of this slice (factor kernel)
+  double sum_xx = 0.0, sum_ee = 0.0;  // running totals (read early; used by the last CTA)
+  long long tcount = 0;
+  if (tid == 0) {
+    sum_xx = a.ctl->sum_xx;
+    sum_ee = a.ctl->sum_ee;
+    tcount = a.ctl->t;
+  }
+  if (a.ctl->skip) {
+    // non-finite slice: the new state is the old one
+    const long long nthr = (long long)gridDim.x * K2_THREADS;
+    const long long me = (long long)blockIdx.x * K2_THREADS + tid;
+    for (long long e = me; e < (long long)M * r; e += nthr) a.Qst[e] = a.Qold[e];
+    for (long long e = me; e < (long long)r * a.J; e += nthr) {
+      a.Cst[e] = a.Cold[e];
+      ((TX*)a.Chst)[e] = ((const TX*)a.Chold)[e];
+    }
+    for (long long e = me; e < rr; e += nthr) a.W2st[e] = a.W2old[e];
+    if (me == 0) *a.ch_shift = *a.ch_shift_old;
+    if (!mbar_wait(smem_u32(&xbar), 0) && tid == 0) a.ctl->latched = 5;
+    return;
+  }
+  // 3. Q1 (all rows, swizzled; rows past I_1 zero) and Nx
+  {
+    const TX* Qh = (const TX*)a.Qh;
+    constexpr int CPR = NP / 8;
+    for (int c = tid; c < Mp * CPR; c += K2_THREADS) {
+      const int row = c / CPR, ch = c % CPR;
+      const bool ok = row < M;
+      cp_async16(qs + qswz<NP>(row, ch), Qh + (ok ? (long long)row * NP + ch * 8 : 0), ok ? 16u : 0u);
+    }
+    for (int e = tid; e < rr; e += K2_THREADS) cp_async4(smem_u32(sN + (e / r) * NP + e % r), a.Nx + e);
+    cp_async_commit();
+    for (int e = tid; e < NP * NP; e += K2_THREADS)
+      if (e / NP >= r || e % NP >= r) sN[e] = 0.f;
+    cp_async_wait<0>();
+  }
+  if (!mbar_wait(smem_u32(&xbar), 0)) timeout_flag = 1;
+  __syncthreads();
+  if (tr0) TTRACE(22);
+  // 4. F^T (j x a) = X^T Q1: warp w takes the k-steps w, w+8, ... for all 64 columns
+  float acc[MT][NT][4];
+#pragma unroll
+  for (int m = 0; m < MT; ++m)
+#pragma unroll
+    for (int n = 0; n < NT; ++n) acc[m][n][0] = acc[m][n][1] = acc[m][n][2] = acc[m][n][3] = 0.f;
+  for (int ks = warp; ks < Mp / 16; ks += K2_THREADS / 32) {
+    const int k0 = ks * 16;
+    uint32_t bq[NT][2];
+#pragma unroll
+    for (int p = 0; p < NT / 2; ++p) {
+      const int row = k0 + (lane & 7) + (((lane >> 3) & 1) << 3);
+      ldsm_x4_t(qs + qswz<NP>(row, 2 * p + (lane >> 4)), bq[2 * p][0], bq[2 * p][1], bq[2 * p + 1][0],
+                bq[2 * p + 1][1]);
+    }
+#pragma unroll
+    for (int m = 0; m < MT; ++m) {
+      uint32_t af[4];
+      const int row = k0 + (lane & 7) + ((lane >> 4) << 3);
+      ldsm_x4_t(xs + swz(row, 2 * m + ((lane >> 3) & 1)), af[0], af[1], af[2], af[3]);
+#pragma unroll
+      for (int n = 0; n < NT; ++n) mma16816<TX>(acc[m][n], af, bq[n][0], bq[n][1]);
+    }
+  }
+  __syncthreads();          // every warp is done with the X block before it becomes RED
+  {
+    const int g = lane >> 2, t4 = lane & 3;
+    float* R = RED + warp * K2S_BN * LDR;
+#pragma unroll
+    for (int m = 0; m < MT; ++m)
+#pragma unroll
+      for (int n = 0; n < NT; ++n) {
+        const int row = m * 16 + g, col = n * 8 + 2 * t4;
+        *reinterpret_cast<float2*>(R + row * LDR + col) = make_float2(acc[m][n][0], acc[m][n][1]);
+        *reinterpret_cast<float2*>(R + (row + 8) * LDR + col) = make_float2(acc[m][n][2], acc[m][n][3]);
+      }
+  }
+  if (tid == 0 && timeout_flag) a.ctl->latched = 5;
+  __syncthreads();
+  for (int o = tid; o < K2S_BN * NP; o += K2_THREADS) {
+    const int jl = o / NP, c = o % NP;
+    float v[K2_THREADS / 32];
+#pragma unroll
+    for (int w = 0; w < K2_THREADS / 32; ++w) v[w] = RED[w * K2S_BN * LDR + jl * LDR + c];
+    float sum = 0.f;
+#pragma unroll
+    for (int w = 0; w < K2_THREADS / 32; ++w) sum += v[w];
+    if (c < r) sF[jl * LDF + c] = sum;
+  }
+  __syncthreads();
+  if (tr0) TTRACE(23);
+  // 5. write F and its ingest-type copy (coalesced along j); ||x^||^2 of my columns
+  int shift = 0;
+  if (a.is_half && xx > 0.0) {
+    const float nrm = sqrtf((float)xx);
+    shift = nrm > 16384.f ? (int)ceilf(log2f(nrm / 16384.f)) : 0;
+  }
+  if (ct == 0 && tid == 0) *a.ch_shift = shift;
+  const float scale = ldexpf(1.0f, -shift);
+  float ph = 0.f, pl = 0.f;     // float-float partial of ||x^||^2
+  env_columns_out<TX, NP>(sF, LDF, sN, xcols, r, a.J, j0, a.Cst, (TX*)a.Chst, scale, ph, pl);
+  const float2 cc_cta = ff_block_sum(ph, pl, redf);
+  if (tr0) TTRACE(24);
+  // one partial per CTA; the last CTA of the grid sums them in a fixed order
+  const int ncta = (int)gridDim.x;
+  if (tid == 0) {
+    a.cc_part[ct] = cc_cta;
+    __threadfence();
+    const unsigned done = atomicAdd(a.counter, 1u);
+    last_flag = (done == (unsigned)ncta - 1u);
+  }
+  __syncthreads();
+  if (!last_flag) return;
+  TTRACE(27);
+  __threadfence();
+  float sh = 0.f, sl = 0.f;
+  for (int b0 = tid; b0 < ncta; b0 += 4 * K2_THREADS) {
+    float2 v[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+      v[u] = (b0 + u * K2_THREADS < ncta) ? __ldcg(a.cc_part + b0 + u * K2_THREADS) : make_float2(0.f, 0.f);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) ff_add(sh, sl, v[u].x, v[u].y);
   }
   const float2 ccf = ff_block_sum(sh, sl, redf);
   if (tid == 0) {
