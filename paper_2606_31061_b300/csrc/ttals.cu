@@ -281,7 +281,7 @@ struct Impl final : ttals_stream {
   float* fY = nullptr;
   float2* fXX = nullptr;       // float-float partials of ||x||^2 (solve CTAs)
   TX* fQh = nullptr;            // Q1 in the ingest type, I_1 x NP (operand of the env kernel)
-  float* fNx = nullptr;         // W2^{-1} - I (r x r)
+  float* fW2part = nullptr;     // [8][NP*NP] W2 partials of the factor kernel's ranks
   float* fQfb = nullptr;
   float2* fCC = nullptr;       // float-float partials of ||x^||^2 (env CTAs)
   bool k2_single = false;       // environment kernel: one CTA per 64-column tile over all rows
@@ -448,7 +448,7 @@ struct Impl final : ttals_stream {
     TT_TRY(dalloc(&fY, (size_t)(M * r)));
     TT_TRY(dalloc(&fXX, (size_t)k1_rows * k1_split));
     TT_TRY(dalloc(&fQh, (size_t)(M * np_)));
-    TT_TRY(dalloc(&fNx, (size_t)r * r));
+    TT_TRY(dalloc(&fW2part, (size_t)fast::KB_CLUSTER * np_ * np_));
     TT_TRY(dalloc(&fQfb, (size_t)(M * r)));
     TT_TRY(dalloc(&fCC, (size_t)k2_cols * k2_nq));
     TT_TRY(dalloc(&fCounter, 2));
@@ -531,8 +531,7 @@ struct Impl final : ttals_stream {
       ab.r = r;
       ab.Qh = fQh;
       ab.Qst = fQ[np];
-      ab.W2st = fW2[np];
-      ab.Nx = fNx;
+      ab.W2part = fW2part;
       ab.hh_work = hh;
       ab.Qfb = fQfb;
       ab.ctl = ctl;
@@ -557,7 +556,7 @@ struct Impl final : ttals_stream {
       a2.J = rest[1];
       a2.rch = k2_rch;
       a2.Qh = fQh;
-      a2.Nx = fNx;
+      a2.W2part = fW2part;
       a2.Cst = fC[np];
       a2.Chst = fCh[np];
       a2.ch_shift = fShift + np;

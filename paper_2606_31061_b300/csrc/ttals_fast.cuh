@@ -449,8 +449,8 @@ __global__ void __launch_bounds__(K1_THREADS, 2)
 //  2. Every rank factors the scaled Gram D W1 D = L L^T (FP32, one warp).
 //  3. Q1 = Y D L^{-T}: each thread forward-substitutes whole rows, z = L^{-1} (D y),
 //     and rounds them to the ingest type (the values that multiply X in the env kernel).
-//  4. W2 = Q1^T Q1 of the rounded rows on tensor cores (exact products), summed over the
-//     ranks; rank q forms rows of Nx = W2^{-1} - I = -D2 + D2^2 - D2^3 (D2 = W2 - I).
+//  4. W2 partial = (my rounded rows)^T (my rounded rows) on tensor cores (exact products),
+//     written to global memory; the environment kernel sums the partials in rank order.
 // A failed factorisation (scaled pivot <= 1e-4: rank-deficient or badly conditioned Y)
 // takes the FP64 Householder QR of Y on rank 0 instead.
 constexpr int K1B_THREADS = 256;
@@ -462,8 +462,7 @@ struct FactorArgs {
   int nxx, M, r;
   void* Qh;               // M x NP ingest-type Q1 (columns >= r zero)
   float* Qst;             // state: Q1 (M x r) as float
-  float* W2st;            // state: W2 (r x r)
-  float* Nx;              // r x r correction of the projector
+  float* W2part;          // [KB_CLUSTER][NP*NP] W2 partials of the ranks' rows
   double* hh_work;        // 2*M*r doubles (fallback)
   float* Qfb;             // M x r (fallback Q, float)
   Ctl* ctl;
@@ -506,6 +505,7 @@ __global__ void __launch_bounds__(K1B_THREADS, 1) k_fast_factor(FactorArgs a) {
   pdl_wait();
   pdl_trigger();
   TTRACE(10);
+  TTRACE_CTA2(0);
   // ---- my rows of Y (asynchronous copies; padding columns r..NP-1 zero)
   if ((r & 3) == 0) {
     const int cpr = r / 4;
@@ -620,6 +620,7 @@ __global__ void __launch_bounds__(K1B_THREADS, 1) k_fast_factor(FactorArgs a) {
     return;
   }
   TTRACE(11);
+  TTRACE_CTA2(1);
   // ---- 2. Cholesky of the scaled Gram: D W1 D = L L^T, stored transposed (LT)
   for (int e = tid; e < NP * LDT; e += K1B_THREADS) LT[e] = 0.f;
   __syncthreads();
@@ -774,6 +775,7 @@ __global__ void __launch_bounds__(K1B_THREADS, 1) k_fast_factor(FactorArgs a) {
     }
   }
   TTRACE(18);
+  TTRACE_CTA2(2);
   __syncthreads();
   // my rows of Q1, coalesced: ingest-type copy (16-byte chunks) and FP32 state
   for (int e = tid; e < myrows * (NP / 8); e += K1B_THREADS) {
@@ -807,77 +809,74 @@ __global__ void __launch_bounds__(K1B_THREADS, 1) k_fast_factor(FactorArgs a) {
       Wp[(row + 8) * NP + col + 1] = acc[3];
     }
   }
-  TTRACE(19);
-  cluster_sync();
-  // W2 = the ranks' partials in rank order (every rank)
-  {
-    const uint32_t wb = smem_u32(Wp);
-    for (int e0 = tid; e0 < rr; e0 += 4 * K1B_THREADS) {
-      float v[4][KB_CLUSTER];
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int e = e0 + u * K1B_THREADS;
-        const int ec = e < rr ? e : rr - 1;            // in-range address; value masked below
-        const uint32_t la = wb + (uint32_t)((ec / r) * NP + ec % r) * 4u;
-#pragma unroll
-        for (int q = 0; q < KB_CLUSTER; ++q) {
-          const float x = dsmem_ld_rank(la, q, KB_CLUSTER);
-          v[u][q] = e < rr ? x : 0.f;
-        }
-      }
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        float hi = 0.f, lo = 0.f;
-#pragma unroll
-        for (int q = 0; q < KB_CLUSTER; ++q) two_sum_acc(hi, lo, v[u][q]);
-        if (e0 + u * K1B_THREADS < rr) W[e0 + u * K1B_THREADS] = hi + lo;
-      }
-    }
-  }
-  cluster_arrive();   // peers may leave once every rank has read my partial (wait at the end)
   __syncthreads();
-  TTRACE(14);
-  // ---- rows [i0, i1) of Nx = -D2 + D2^2 - D2^3 (D2 = W2 - I): U = D2 rows x D2, V = U x D2
-  {
-    const int rpb = (r + KB_CLUSTER - 1) / KB_CLUSTER;
-    const int i0 = (int)crank * rpb, i1 = (i0 + rpb < r) ? i0 + rpb : r;
-    const int nr = i1 > i0 ? i1 - i0 : 0;
-    float* U = Gr;                   // nr x r
-    for (int e = tid; e < nr * r; e += K1B_THREADS) {
-      const int i = i0 + e / r, j = e % r;
-      float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
-      int k = 0;
-      for (; k + 3 < r; k += 4) {
-        s0 = fmaf(W[i * r + k] - (i == k ? 1.f : 0.f), W[k * r + j] - (k == j ? 1.f : 0.f), s0);
-        s1 = fmaf(W[i * r + k + 1] - (i == k + 1 ? 1.f : 0.f), W[(k + 1) * r + j] - (k + 1 == j ? 1.f : 0.f), s1);
-        s2 = fmaf(W[i * r + k + 2] - (i == k + 2 ? 1.f : 0.f), W[(k + 2) * r + j] - (k + 2 == j ? 1.f : 0.f), s2);
-        s3 = fmaf(W[i * r + k + 3] - (i == k + 3 ? 1.f : 0.f), W[(k + 3) * r + j] - (k + 3 == j ? 1.f : 0.f), s3);
-      }
-      for (; k < r; ++k) s0 = fmaf(W[i * r + k] - (i == k ? 1.f : 0.f), W[k * r + j] - (k == j ? 1.f : 0.f), s0);
-      U[e] = (s0 + s1) + (s2 + s3);
-    }
-    __syncthreads();
-    for (int e = tid; e < nr * r; e += K1B_THREADS) {
-      const int i = i0 + e / r, j = e % r;
-      const float* ur = U + (e / r) * r;
-      float v0 = 0.f, v1 = 0.f, v2 = 0.f, v3 = 0.f;
-      int k = 0;
-      for (; k + 3 < r; k += 4) {
-        v0 = fmaf(ur[k], W[k * r + j] - (k == j ? 1.f : 0.f), v0);
-        v1 = fmaf(ur[k + 1], W[(k + 1) * r + j] - (k + 1 == j ? 1.f : 0.f), v1);
-        v2 = fmaf(ur[k + 2], W[(k + 2) * r + j] - (k + 2 == j ? 1.f : 0.f), v2);
-        v3 = fmaf(ur[k + 3], W[(k + 3) * r + j] - (k + 3 == j ? 1.f : 0.f), v3);
-      }
-      for (; k < r; ++k) v0 = fmaf(ur[k], W[k * r + j] - (k == j ? 1.f : 0.f), v0);
-      const float v = (v0 + v1) + (v2 + v3);
-      const float d2 = W[i * r + j] - (i == j ? 1.f : 0.f);
-      a.Nx[i * r + j] = -d2 + U[e] - v;
-      a.W2st[i * r + j] = W[i * r + j];
-    }
-    if (tid == 0 && crank == 0 && fb) a.ctl->fallback[0] = 1;
-  }
-  cluster_wait();
+  TTRACE(19);
+  // this rank's W2 partial (its rows of Q1) to global memory; the environment kernel sums
+  // the ranks' partials in rank order and forms Nx = W2^{-1} - I itself
+  for (int e = tid; e < NP * NP; e += K1B_THREADS) a.W2part[(size_t)crank * NP * NP + e] = Wp[e];
+  if (tid == 0 && crank == 0 && fb) a.ctl->fallback[0] = 1;
   TTRACE(15);
+  TTRACE_CTA2(3);
+}
+
+constexpr int K2_THREADS = 256;
+constexpr int K2_BN = 128;            // slice columns j per CTA of the clustered env kernel
+
+// W2 = sum over the factor kernel's ranks (rank order, TwoSum) of its NP x NP partials; the
+// state's W2 (r x r) is written when `write_state`.  sD receives D2 = W2 - I zero-padded to
+// NP x NP and sN receives Nx = W2^{-1} - I = -D2 + D2^2 (|D2| ~ 1e-3 for a rounded
+// orthonormal basis, so the D2^3 term is below 1e-8), zero past r.  D2^2 is a fully unrolled
+// 2 x 2 register-blocked product.  All K2_THREADS threads; ends synchronised.
+template <int NP>
+__device__ __forceinline__ void env_w2_nx(const float* __restrict__ W2part, int r, float* sD, float* sN,
+                                          float* W2st, bool write_state) {
+  const int tid = threadIdx.x;
+  constexpr int PER = (NP * NP + K2_THREADS - 1) / K2_THREADS;
+  constexpr int G = PER < 4 ? PER : 4;       // elements whose partials are loaded together
+  for (int u0 = 0; u0 < PER; u0 += G) {
+  float v[G][KB_CLUSTER];
+#pragma unroll
+  for (int u = 0; u < G; ++u) {
+    const int e = tid + (u0 + u) * K2_THREADS;
+    const int ec = e < NP * NP ? e : NP * NP - 1;
+#pragma unroll
+    for (int q = 0; q < KB_CLUSTER; ++q) v[u][q] = __ldcg(W2part + (size_t)q * NP * NP + ec);
+  }
+#pragma unroll
+  for (int u = 0; u < G; ++u) {
+    const int e = tid + (u0 + u) * K2_THREADS;
+    if (e < NP * NP) {
+      const int i = e / NP, j = e % NP;
+      float hi = 0.f, lo = 0.f;
+#pragma unroll
+      for (int q = 0; q < KB_CLUSTER; ++q) two_sum_acc(hi, lo, v[u][q]);
+      const float w = hi + lo;
+      const bool in = i < r && j < r;
+      sD[e] = in ? w - (i == j ? 1.f : 0.f) : 0.f;
+      if (write_state && in) W2st[i * r + j] = w;
+    }
+  }
+  }
+  __syncthreads();
+  constexpr int HB = NP / 2;
+  for (int blk = tid; blk < HB * HB; blk += K2_THREADS) {
+    const int i0 = 2 * (blk / HB), j0 = 2 * (blk % HB);
+    float c00 = 0.f, c01 = 0.f, c10 = 0.f, c11 = 0.f;
+#pragma unroll
+    for (int k = 0; k < NP; ++k) {
+      const float a0 = sD[i0 * NP + k], a1 = sD[(i0 + 1) * NP + k];
+      const float2 bk = *reinterpret_cast<const float2*>(sD + k * NP + j0);
+      c00 = fmaf(a0, bk.x, c00);
+      c01 = fmaf(a0, bk.y, c01);
+      c10 = fmaf(a1, bk.x, c10);
+      c11 = fmaf(a1, bk.y, c11);
+    }
+    *reinterpret_cast<float2*>(sN + i0 * NP + j0) =
+        make_float2(c00 - sD[i0 * NP + j0], c01 - sD[i0 * NP + j0 + 1]);
+    *reinterpret_cast<float2*>(sN + (i0 + 1) * NP + j0) =
+        make_float2(c10 - sD[(i0 + 1) * NP + j0], c11 - sD[(i0 + 1) * NP + j0 + 1]);
+  }
+  __syncthreads();
 }
 
 // ||x^||^2 terms f_c (f + Nx f)_c of the columns of an F tile held as sF[jl*ldf + c] (c < r),
@@ -922,15 +921,12 @@ __device__ __forceinline__ void env_columns_out(const float* sF, int ldf, const 
 // cluster and reduce through distributed shared memory.  Writes F (the state's right
 // part) and its scaled ingest-type copy, and the step's ||x^||^2 = sum_j f_j^T (I + Nx) f_j.
 // The X block arrives as two 64-column, 128B-swizzled TMA boxes of rch rows.
-constexpr int K2_THREADS = 256;
-constexpr int K2_BN = 128;            // slice columns j per CTA
-
 struct EnvArgs {
   int M, r;
   long long J;
   int rch;              // rows per cluster rank (multiple of 16)
   const void* Qh;       // M x NP ingest-type Q1
-  const float* Nx;      // r x r
+  const float* W2part;  // [KB_CLUSTER][NP*NP] W2 partials of the factor kernel's ranks
   float* Cst;           // state: F (r x J)
   void* Chst;           // state: scaled ingest-type copy of F (r x J)
   int* ch_shift;        // state: power-of-two scale exponent of Chst
@@ -950,9 +946,10 @@ struct EnvArgs {
 
 template <int NP>
 constexpr size_t k2_smem_bytes(int rch, int r) {
-  // X block (2 x rch x 128 B) | Q1 tile | partial tile P (BN x (NP+8)) | my columns F | Nx (NP x NP)
+  // X block (2 x rch x 128 B) | Q1 tile | partial tile P (BN x (NP+8)) | my columns F |
+  // Nx (NP x NP) | W2 (NP x NP)
   return 1024 + (size_t)rch * 256 + (size_t)rch * (NP + 8) * 2 + (size_t)K2_BN * (NP + 8) * 4 +
-         (size_t)K2_BN * (r + 1) * 4 + (size_t)NP * NP * 4 + 64;
+         (size_t)K2_BN * (r + 1) * 4 + (size_t)2 * NP * NP * 4 + 64;
 }
 
 template <typename TX, int NP>
@@ -968,7 +965,8 @@ __global__ void __launch_bounds__(K2_THREADS, 2)
   float* P = reinterpret_cast<float*>(sQ + (size_t)rch * (NP + 8));  // [BN][NP+8]
   const int LDF = r + 1;                                             // padded: conflict-free
   float* sF = P + K2_BN * LDP;                                       // [BN][r+1] (my columns)
-  float* sN = sF + K2_BN * LDF;                                      // Nx
+  float* sN = sF + K2_BN * LDF;                                      // Nx (NP x NP)
+  float* sW = sN + NP * NP;                                          // D2 = W2 - I (NP x NP)
   __shared__ __align__(8) uint64_t xbar;
   __shared__ float redf[64];
   __shared__ int last_flag;
@@ -982,6 +980,7 @@ __global__ void __launch_bounds__(K2_THREADS, 2)
   const int i0 = (int)crank * rch;
   const int xcols = (a.J - j0 < K2_BN) ? (int)(a.J - j0) : K2_BN;
   const bool tr0 = (blockIdx.x == 0 && blockIdx.y == 0);
+  const bool W2_WRITER = (blockIdx.x == 0 && blockIdx.y == 0);   // one CTA writes the state's W2
 
   // 1. this CTA's X block through the TMA engine (independent of the previous kernels)
   if (tid == 0) {
@@ -1030,10 +1029,8 @@ __global__ void __launch_bounds__(K2_THREADS, 2)
       const bool ok = gi < a.M;
       cp_async16(smem_u32(sQ + row * (NP + 8) + ch * 8), Qh + (ok ? (long long)gi * NP + ch * 8 : 0), ok ? 16u : 0u);
     }
-    for (int e = tid; e < rr; e += K2_THREADS) cp_async4(smem_u32(sN + (e / r) * NP + e % r), a.Nx + e);
     cp_async_commit();
-    for (int e = tid; e < NP * NP; e += K2_THREADS)
-      if (e / NP >= r || e % NP >= r) sN[e] = 0.f;
+    env_w2_nx<NP>(a.W2part, r, sW, sN, a.W2st, W2_WRITER);
     cp_async_wait<0>();
   }
   if (!mbar_wait(smem_u32(&xbar), 0)) timeout_flag = 1;
@@ -1188,7 +1185,7 @@ __host__ __device__ constexpr int k2s_boxes(int M) { return (M + 255) / 256; }
 template <int NP>
 __host__ __device__ constexpr size_t k2s_smem_bytes(int M, int r) {
   return 1024 + (size_t)k2s_boxes(M) * k2s_box_rows(M) * 128 + (size_t)((M + 15) / 16 * 16) * NP * 2 +
-         (size_t)NP * NP * 4 + 64 + 0 * r;
+         (size_t)2 * NP * NP * 4 + 64 + 0 * r;
 }
 // the warp partials (8 x 64 x (NP+8)) and my columns of F (64 x (r+1)) reuse the X block
 template <int NP>
@@ -1212,6 +1209,7 @@ __global__ void __launch_bounds__(K2_THREADS, 1)
   unsigned char* qbase = smem + (size_t)NBX * RB * 128;               // Q1, swizzled
   const uint32_t qs = smem_u32(qbase);
   float* sN = reinterpret_cast<float*>(qbase + (size_t)Mp * NP * 2);  // Nx, NP x NP, zero past r
+  float* sW = sN + NP * NP;                                            // D2 = W2 - I (NP x NP)
   constexpr int LDR = NP + 8;                                          // float2 stores: 2 wavefronts
   float* RED = reinterpret_cast<float*>(smem);                        // [8][64][NP+8] after the product
   const int LDF = r + 1;
@@ -1226,6 +1224,7 @@ __global__ void __launch_bounds__(K2_THREADS, 1)
   const long long j0 = (long long)ct * K2S_BN;
   const int xcols = (a.J - j0 < K2S_BN) ? (int)(a.J - j0) : K2S_BN;
   const bool tr0 = (blockIdx.x == 0);
+  const bool W2_WRITER = (blockIdx.x == 0);   // one CTA writes the state's W2
 
   // 1. this CTA's X block through the TMA engine (independent of the previous kernels)
   if (tid == 0) {
@@ -1273,10 +1272,8 @@ __global__ void __launch_bounds__(K2_THREADS, 1)
       const bool ok = row < M;
       cp_async16(qs + qswz<NP>(row, ch), Qh + (ok ? (long long)row * NP + ch * 8 : 0), ok ? 16u : 0u);
     }
-    for (int e = tid; e < rr; e += K2_THREADS) cp_async4(smem_u32(sN + (e / r) * NP + e % r), a.Nx + e);
     cp_async_commit();
-    for (int e = tid; e < NP * NP; e += K2_THREADS)
-      if (e / NP >= r || e % NP >= r) sN[e] = 0.f;
+    env_w2_nx<NP>(a.W2part, r, sW, sN, a.W2st, W2_WRITER);
     cp_async_wait<0>();
   }
   if (!mbar_wait(smem_u32(&xbar), 0)) timeout_flag = 1;
