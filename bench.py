@@ -230,6 +230,60 @@ def time_arm(ingest, steps, warmup, pool, dist_on, sampler_idx):
                 lat=lat, clocks=clocks, re=math.sqrt(stats[3] / stats[2]) if stats[2] > 0 else None)
 
 
+def batched_arm(ingest, nstreams, steps, warmup, pool):
+    """`nstreams` independent video streams stepped together (ttals_push_batch): each push
+    carries one slice per stream, contiguous [nstreams][slice].  Stream b at step t reads
+    pool frame o_t + b, with o_t walking the pool forward and backward, so that every
+    stream stays temporally smooth.  Returns device time, per-kernel times, per-push latency
+    and each stream's relative reconstruction error."""
+    import torch
+    from paper_2606_31061_b300.ttals import Stream
+    st = Stream(DIMS, RANKS, ingest=ingest, n_streams=nstreams)
+    P = pool.shape[0]
+    W = P - nstreams + 1
+    stream = torch.cuda.current_stream()
+    h = stream.cuda_stream
+    ptrs = [pool[o].data_ptr() for o in range(W)]
+    for t in range(warmup):
+        st.push_batch_ptr(ptrs[pingpong(t, W)], h)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda._sleep(int(2e8))
+    n0 = st.launch_count
+    e0.record(stream)
+    for t in range(steps):
+        st.push_batch_ptr(ptrs[pingpong(warmup + t, W)], h)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    launches = st.launch_count - n0
+    nprof = min(steps, 200)
+    st.profile(True)
+    torch.cuda._sleep(int(2e8))
+    for t in range(nprof):
+        st.push_batch_ptr(ptrs[pingpong(warmup + steps + t, W)], h)
+    ms_solve, ms_factor, ms_env, ms_push, npush = st.profile_read()
+    st.profile(False)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(min(steps, 200))]
+    torch.cuda._sleep(int(2e8))
+    for t, (a, b) in enumerate(ev):
+        a.record(stream)
+        st.push_batch_ptr(ptrs[pingpong(warmup + steps + nprof + t, W)], h)
+        b.record(stream)
+    torch.cuda.synchronize()
+    lat = sorted(a.elapsed_time(b) for a, b in ev)
+    res = []
+    for b in range(nstreams):
+        st.select(b)
+        s = st.stats()
+        res.append(math.sqrt(s[3] / s[2]) if s[2] > 0 else float("nan"))
+    st.close()
+    return dict(ms=ms, launches=launches, ms_solve=ms_solve, ms_factor=ms_factor, ms_env=ms_env,
+                ms_push=ms_push, npush=npush, lat=lat, re=res)
+
+
 def e2e_arm(ingest, steps, pool_np, dist_on):
     """Same metric through the C ABI from pinned HOST buffers: per step an H2D copy of the
     slice (copy stream, double-buffered device slot), the push, and an async D2H read of
@@ -332,6 +386,8 @@ def main():
     ap.add_argument("--no-f32", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=300)
+    ap.add_argument("--batch", type=int, default=16, help="streams per batched push (0: skip)")
+    ap.add_argument("--batch-steps", type=int, default=400)
     args = ap.parse_args()
     rank = env_int("RANK", 0)
     world = env_int("WORLD_SIZE", 1)
@@ -384,6 +440,35 @@ def main():
         t = torch.tensor([e2e_sec], device="cuda")
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         e2e_sec = float(t.item())
+    batched = None
+    if args.batch > 0:
+        S = min(args.batch, args.pool)
+        rb = batched_arm(args.ingest, S, args.batch_steps, args.warmup, pool)
+        bsec = rb["ms"] / 1000.0
+        if dist_on:
+            t = torch.tensor([bsec], device="cuda")
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            bsec = float(t.item())
+        nb = max(1, rb["npush"])
+        bper = {"solve": rb["ms_solve"] / nb, "factor": rb["ms_factor"] / nb, "env": rb["ms_env"] / nb}
+        bdom = max(bper, key=bper.get)
+        blat = rb["lat"]
+        bach = {k: S * alg[k] / (bper[k] * 1e-3) / 1e9 for k in bper}
+        batched = {
+            "streams": S, "steps": args.batch_steps,
+            "value": args.batch_steps * S * world / bsec, "unit": "slices/s",
+            "ms_per_step": rb["ms"] / args.batch_steps,
+            "hbm_gbs": args.batch_steps * S * world / bsec * slice_bytes / 1e9,
+            "gpu_launches": rb["launches"],
+            "latency_ms": {"p50": blat[len(blat) // 2], "p99": blat[min(len(blat) - 1, int(0.99 * len(blat)))],
+                           "n": len(blat), "what": "one batched push (every stream's slice of that step)"},
+            "re_per_stream": {"min": min(rb["re"]), "max": max(rb["re"])},
+            "roofline": {"bound": "hbm", "kernel": bdom, "achieved": bach[bdom], "peak": peak,
+                         "peak_source": peak_src, "unit": "GB/s", "frac": bach[bdom] / peak,
+                         "algorithmic_bytes": S * alg[bdom], "ms_per_launch": bper[bdom],
+                         "achieved_all": bach, "ms_per_launch_all": bper},
+            "inputs": f"stream b at step t reads pool frame o_t + b; one push reads {S * slice_bytes / 1e6:.0f} MB",
+        }
     f32 = None
     if not args.no_f32 and args.ingest != "f32":
         del pool
@@ -429,6 +514,7 @@ def main():
                     "h2d_bytes_per_step": e2e["h2d"], "d2h_bytes_per_step": e2e["d2h"]},
             "gpu_launches": r["launches"],
             "clocks": r["clocks"],
+            "batched": batched,
             "f32_ingest": f32,
             "cpu_baseline": cpu,
         }

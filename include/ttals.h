@@ -192,6 +192,40 @@ ttals_status ttals_slice_error_noalloc(const void *x_dev, ttals_dtype x_dtype, c
                                        ttals_dtype y_dtype, int64_t n, double *out2_dev,
                                        void *cuda_stream);
 
+/*
+ * Batches of streams.  Algorithm 1 updates one stream; a batch holds n_streams
+ * independent streams of ONE shape (dims, ranks, ingest) whose updates run in the
+ * same kernel launches (each launch's grid gains one plane per stream), so that a
+ * step of many small streams reads their slices at full HBM rate.  Every stream of
+ * a batch computes exactly what it computes alone: the same kernels, the same
+ * reduction orders, bitwise the same results.
+ *
+ * ttals_create_batch - like ttals_create, for 1 <= n_streams <= TTALS_MAX_BATCH
+ *   streams.  Stream b starts from its own default cores (the b-th draw of the
+ *   seeded generator; stream 0's equal ttals_create's).  Only shapes that take the
+ *   fused FP16/BF16 path batch: FP16/BF16 ingest, r_1 >= I_2...I_{n-1} (saturated
+ *   second level), r_1 <= 64, I_2...I_{n-1} a multiple of 8, I_1 <= 4096.
+ *   Errors: EINVAL (also for a shape that does not batch; message in
+ *   ttals_last_error), ENOMEM, ECUDA.
+ * ttals_push_batch - one step of every stream of the batch.  slices_dev holds
+ *   n_streams slices back to back ([n_streams][I_1]...[I_{n-1}], C order, stream b's
+ *   slice at element offset b * I_1...I_{n-1}), 16-byte aligned, device memory
+ *   owned by the caller and kept alive until the work on cuda_stream passes the
+ *   call.  Asynchronous.  Errors: EINVAL, ECUDA.
+ * ttals_batch_select - wait for the batch's work, then direct the per-stream calls
+ *   (ttals_set_cores, ttals_cores, ttals_reconstruct, ttals_stats, ttals_stats_async,
+ *   ttals_step, ttals_sync) to stream `index`.  Errors: EINVAL, ECUDA.
+ * ttals_batch_size - n_streams of a batch, 1 for a single stream, 0 for NULL.
+ * ttals_push_slice on a batch returns ESTATE.
+ */
+#define TTALS_MAX_BATCH 64
+ttals_status ttals_create_batch(int n_streams, int n_slice_modes, const int64_t *dims,
+                                const int64_t *ranks, const ttals_config *cfg, ttals_stream **out);
+ttals_status ttals_push_batch(ttals_stream *s, const void *slices_dev, ttals_dtype dtype,
+                              void *cuda_stream);
+ttals_status ttals_batch_select(ttals_stream *s, int index);
+int ttals_batch_size(const ttals_stream *s);
+
 /* Static text for a status code. */
 const char *ttals_status_string(ttals_status st);
 

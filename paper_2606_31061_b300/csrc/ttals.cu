@@ -115,16 +115,18 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
   return fn;
 }
 
-// 2-D map of a row-major rows x cols matrix of 16-bit elements, box (64 cols) x box_rows,
-// 128-byte swizzle, out-of-range elements read as zero
-bool encode_map_2d(CUtensorMap* map, const void* base, bool bf16, long long rows, long long cols, int box_rows) {
+// 3-D map of nplanes contiguous row-major rows x cols matrices of 16-bit elements (plane z of
+// a batch is stream z's matrix), box (64 cols) x box_rows x 1 plane, 128-byte swizzle;
+// out-of-range elements (rows >= rows of a plane included) read as zero
+bool encode_map_3d(CUtensorMap* map, const void* base, bool bf16, long long nplanes, long long rows, long long cols,
+                   int box_rows) {
   PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
   if (!enc) return false;
-  cuuint64_t dim[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
-  cuuint64_t stride[1] = {(cuuint64_t)cols * 2};
-  cuuint32_t box[2] = {64u, (cuuint32_t)box_rows};
-  cuuint32_t estr[2] = {1u, 1u};
-  CUresult r = enc(map, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2,
+  cuuint64_t dim[3] = {(cuuint64_t)cols, (cuuint64_t)rows, (cuuint64_t)nplanes};
+  cuuint64_t stride[2] = {(cuuint64_t)cols * 2, (cuuint64_t)(rows * cols) * 2};
+  cuuint32_t box[3] = {64u, (cuuint32_t)box_rows, 1u};
+  cuuint32_t estr[3] = {1u, 1u, 1u};
+  CUresult r = enc(map, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 3,
                    const_cast<void*>(base), dim, stride, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                    CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS;
@@ -157,7 +159,10 @@ struct ttals_stream {
   cudaStream_t last = nullptr;
   bool have_last = false;
   cudaEvent_t ev = nullptr;
-  Ctl* ctl = nullptr;
+  Ctl* ctl = nullptr;                 // control block of the selected stream (ctl_base + sel)
+  Ctl* ctl_base = nullptr;            // [nbatch] control blocks
+  int nbatch = 1;                     // streams of a batch (ttals_create_batch), else 1
+  int sel = 0;                        // stream that the per-stream calls refer to
   size_t bytes = 0;
   std::vector<void*> allocs;
   unsigned long long nlaunch = 0;      // kernels launched by this stream (host counter)
@@ -194,6 +199,9 @@ struct ttals_stream {
   virtual ttals_status set_cores(const double* const* cores, const double* g, long long t) = 0;
   virtual ttals_status get_core(int k, double* host, size_t n) = 0;
   virtual ttals_status allocate() = 0;
+  // batches: only the fused path steps several streams per launch
+  virtual bool batch_capable() const { return false; }
+  virtual ttals_status select_slot(int idx) { return idx == 0 ? TTALS_OK : TTALS_EINVAL; }
 
   long long slice_elems() const { return rest[0]; }
   long long core_elems(int k) const {   // k = 1..m
@@ -272,11 +280,18 @@ struct Impl final : ttals_stream {
   int k1_rows = 0, k1_split = 1, k2_cols = 0, k2_nq = 1, k2_rch = 16;
   long long k1_kchunk = 64;
   size_t k1_smem = 0, k2_smem = 0;
-  float* fQ[2] = {};            // Q1 (I_1 x r)
-  float* fC[2] = {};            // F = Q1^T X (r x rest_1): right part of the state
-  TX* fCh[2] = {};              // ingest-type copy of F (scaled by 2^-shift)
-  float* fW2[2] = {};           // Q1^T Q1
-  int* fShift = nullptr;        // [2]
+  // state slabs [nbatch][...] and views of the selected stream's slab
+  float* fQb[2] = {};           // Q1 (I_1 x r)
+  float* fCb[2] = {};           // F = Q1^T X (r x rest_1): right part of the state
+  TX* fChb[2] = {};             // ingest-type copy of F (scaled by 2^-shift)
+  float* fW2b[2] = {};          // Q1^T Q1
+  int* fShiftb = nullptr;       // [nbatch][2]
+  float* fQ[2] = {};
+  float* fC[2] = {};
+  TX* fCh[2] = {};
+  float* fW2[2] = {};
+  int* fShift = nullptr;
+  double* fHH = nullptr;        // [nbatch][2 I_1 r] Householder work of the factor kernel's fallback
   bool finalized[2] = {true, true};
   float* fY = nullptr;
   float2* fXX = nullptr;       // float-float partials of ||x||^2 (solve CTAs)
@@ -285,8 +300,8 @@ struct Impl final : ttals_stream {
   float* fQfb = nullptr;
   float2* fCC = nullptr;       // float-float partials of ||x^||^2 (env CTAs)
   bool k2_single = false;       // environment kernel: one CTA per 64-column tile over all rows
-  unsigned* fCounter = nullptr; // [2]
-  CUtensorMap mapB[2];          // TMA maps of fCh[p] (r x rest_1, box 64 x NP)
+  unsigned* fCounter = nullptr; // [nbatch][2]
+  CUtensorMap mapB[2];          // TMA maps of fChb[p] (nbatch x r x rest_1, box 64 x NP)
 
   int rows(int k) const { return (int)(full[k - 1] * dims[k - 1]); }  // r_{k-1} I_k
   int rk(int k) const { return (int)full[k]; }
@@ -342,8 +357,9 @@ struct Impl final : ttals_stream {
     size_t maxcore = 0;
     for (int k = 1; k <= m; ++k) maxcore = std::max<size_t>(maxcore, (size_t)core_elems(k));
     TT_TRY(dalloc(&dout, maxcore));
-    TT_TRY(dalloc(&ctl, 1));
-    TT_CUDA(cudaMemset(ctl, 0, sizeof(Ctl)));
+    TT_TRY(dalloc(&ctl, (size_t)nbatch));
+    TT_CUDA(cudaMemset(ctl, 0, sizeof(Ctl) * nbatch));
+    ctl_base = ctl;
     TT_CUDA(cudaFuncSetAttribute(k_factor, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024));
     TT_CUDA(cudaFuncSetAttribute(fast::k_chol64_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024));
     TT_TRY(setup_fast());
@@ -438,27 +454,51 @@ struct Impl final : ttals_stream {
       case 48: TT_TRY(set_fast_attrs<48>()); break;
       default: TT_TRY(set_fast_attrs<64>()); break;
     }
+    // every buffer below is a slab of nbatch per-stream parts; the kernels offset by blockIdx.z
+    const size_t S = (size_t)nbatch;
     for (int p = 0; p < 2; ++p) {
-      TT_TRY(dalloc(&fQ[p], (size_t)(M * r)));
-      TT_TRY(dalloc(&fC[p], (size_t)(r * J)));
-      TT_TRY(dalloc(&fCh[p], (size_t)(r * J)));
-      TT_TRY(dalloc(&fW2[p], (size_t)(r * r)));
+      TT_TRY(dalloc(&fQb[p], S * M * r));
+      TT_TRY(dalloc(&fCb[p], S * r * J));
+      TT_TRY(dalloc(&fChb[p], S * r * J));
+      TT_TRY(dalloc(&fW2b[p], S * r * r));
     }
-    TT_TRY(dalloc(&fShift, 2));
-    TT_TRY(dalloc(&fY, (size_t)(M * r)));
-    TT_TRY(dalloc(&fXX, (size_t)k1_rows * k1_split));
-    TT_TRY(dalloc(&fQh, (size_t)(M * np_)));
-    TT_TRY(dalloc(&fW2part, (size_t)fast::KB_CLUSTER * np_ * np_));
-    TT_TRY(dalloc(&fQfb, (size_t)(M * r)));
-    TT_TRY(dalloc(&fCC, (size_t)k2_cols * k2_nq));
-    TT_TRY(dalloc(&fCounter, 2));
-    TT_CUDA(cudaMemset(fCounter, 0, 2 * sizeof(unsigned)));
+    TT_TRY(dalloc(&fShiftb, S * 2));
+    TT_TRY(dalloc(&fY, S * M * r));
+    TT_TRY(dalloc(&fXX, S * k1_rows * k1_split));
+    TT_TRY(dalloc(&fQh, S * M * np_));
+    TT_TRY(dalloc(&fW2part, S * fast::KB_CLUSTER * np_ * np_));
+    TT_TRY(dalloc(&fQfb, S * M * r));
+    TT_TRY(dalloc(&fHH, S * 2 * M * r));
+    TT_TRY(dalloc(&fCC, S * k2_cols * k2_nq));
+    TT_TRY(dalloc(&fCounter, S * 2));
+    TT_CUDA(cudaMemset(fCounter, 0, S * 2 * sizeof(unsigned)));
     const bool bf = std::is_same<TX, __nv_bfloat16>::value;
     for (int p = 0; p < 2; ++p)
-      if (!encode_map_2d(&mapB[p], fCh[p], bf, r, J, np_)) return TTALS_OK;
-    TT_CUDA(cudaMemset(fShift, 0, 2 * sizeof(int)));
-    hh_elems = std::max<size_t>(hh_elems, (size_t)(2 * M * r));
+      if (!encode_map_3d(&mapB[p], fChb[p], bf, nbatch, r, J, np_)) return TTALS_OK;
+    TT_CUDA(cudaMemset(fShiftb, 0, S * 2 * sizeof(int)));
     fast = true;
+    return select_slot(0);
+  }
+
+  bool batch_capable() const override { return fast; }
+
+  // point the per-stream views (state, control block) at stream idx of the batch
+  ttals_status select_slot(int idx) override {
+    if (idx < 0 || idx >= nbatch) return TTALS_EINVAL;
+    sel = idx;
+    ctl = ctl_base + idx;
+    if (fast) {
+      const size_t M = (size_t)dims[0], J = (size_t)rest[1], r = (size_t)rk(1);
+      for (int p = 0; p < 2; ++p) {
+        fQ[p] = fQb[p] + idx * M * r;
+        fC[p] = fCb[p] + idx * r * J;
+        fCh[p] = fChb[p] + idx * r * J;
+        fW2[p] = fW2b[p] + idx * r * r;
+      }
+      fShift = fShiftb + 2 * idx;
+      finalized[0] = finalized[1] = false;
+    }
+    materialised = false;
     return TTALS_OK;
   }
 
@@ -474,8 +514,8 @@ struct Impl final : ttals_stream {
     if (map_cache.size() >= kMapCacheCap) map_cache.clear();
     SliceMaps sm;
     const bool bf = std::is_same<TX, __nv_bfloat16>::value;
-    if (!encode_map_2d(&sm.m[0], X, bf, dims[0], rest[1], fast::K1_BM) ||
-        !encode_map_2d(&sm.m[1], X, bf, dims[0], rest[1], k2_rch))
+    if (!encode_map_3d(&sm.m[0], X, bf, nbatch, dims[0], rest[1], fast::K1_BM) ||
+        !encode_map_3d(&sm.m[1], X, bf, nbatch, dims[0], rest[1], k2_rch))
       return nullptr;
     return map_cache.emplace((const void*)X, sm).first->second.m;
   }
@@ -510,9 +550,9 @@ struct Impl final : ttals_stream {
       a1.kchunk = k1_kchunk;
       a1.Y = fY;
       a1.xx_part = fXX;
-      a1.ctl = ctl;
+      a1.ctl = ctl_base;
       cudaLaunchConfig_t c1{};
-      c1.gridDim = dim3((unsigned)k1_rows, (unsigned)k1_split, 1);
+      c1.gridDim = dim3((unsigned)k1_rows, (unsigned)k1_split, (unsigned)nbatch);
       c1.blockDim = dim3(fast::K1_THREADS, 1, 1);
       c1.dynamicSmemBytes = k1_smem;
       c1.stream = s;
@@ -530,17 +570,17 @@ struct Impl final : ttals_stream {
       ab.M = (int)dims[0];
       ab.r = r;
       ab.Qh = fQh;
-      ab.Qst = fQ[np];
+      ab.Qst = fQb[np];
       ab.W2part = fW2part;
-      ab.hh_work = hh;
+      ab.hh_work = fHH;
       ab.Qfb = fQfb;
-      ab.ctl = ctl;
+      ab.ctl = ctl_base;
       cudaLaunchAttribute atb[2];
       atb[0] = at[0];
       atb[0].val.clusterDim.y = (unsigned)fast::KB_CLUSTER;
       atb[1] = at[1];
       cudaLaunchConfig_t cb{};
-      cb.gridDim = dim3(1, (unsigned)fast::KB_CLUSTER, 1);
+      cb.gridDim = dim3(1, (unsigned)fast::KB_CLUSTER, (unsigned)nbatch);
       cb.blockDim = dim3(fast::K1B_THREADS, 1, 1);
       cb.dynamicSmemBytes = fast::k1b_smem_bytes((int)dims[0], r, NP);
       cb.stream = s;
@@ -557,23 +597,23 @@ struct Impl final : ttals_stream {
       a2.rch = k2_rch;
       a2.Qh = fQh;
       a2.W2part = fW2part;
-      a2.Cst = fC[np];
-      a2.Chst = fCh[np];
-      a2.ch_shift = fShift + np;
+      a2.Cst = fCb[np];
+      a2.Chst = fChb[np];
+      a2.ch_shift = fShiftb + np;
       a2.cc_part = fCC;
       a2.counter = fCounter + 1;
-      a2.ctl = ctl;
-      a2.Qst = fQ[np];
-      a2.W2st = fW2[np];
-      a2.Qold = fQ[par];
-      a2.Cold = fC[par];
-      a2.Chold = fCh[par];
-      a2.W2old = fW2[par];
-      a2.ch_shift_old = fShift + par;
+      a2.ctl = ctl_base;
+      a2.Qst = fQb[np];
+      a2.W2st = fW2b[np];
+      a2.Qold = fQb[par];
+      a2.Cold = fCb[par];
+      a2.Chold = fChb[par];
+      a2.W2old = fW2b[par];
+      a2.ch_shift_old = fShiftb + par;
       a2.is_half = std::is_same<TX, __half>::value ? 1 : 0;
       at[0].val.clusterDim.y = (unsigned)k2_nq;
       cudaLaunchConfig_t c2{};
-      c2.gridDim = dim3((unsigned)k2_cols, (unsigned)k2_nq, 1);
+      c2.gridDim = dim3((unsigned)k2_cols, (unsigned)k2_nq, (unsigned)nbatch);
       c2.blockDim = dim3(fast::K2_THREADS, 1, 1);
       c2.dynamicSmemBytes = k2_smem;
       c2.stream = s;
@@ -629,8 +669,14 @@ struct Impl final : ttals_stream {
       if (!fast) return TTALS_OK;
       const int r = rk(1);
       const long long M = dims[0], J = rest[1];
+      static_assert(std::is_same<TC, float>::value, "the fused path keeps FP32 state");
       TT_CUDA(cudaMemcpyAsync(fQ[par], G[par][0], (size_t)(M * r) * 4, cudaMemcpyDeviceToDevice, s));
-      TT_CUDA(cudaMemcpyAsync(fC[par], C[par], (size_t)(r * J) * 4, cudaMemcpyDeviceToDevice, s));
+      // W2 = G1^T G1 and F = W2 C: the fused state (Q1, W2, F) stands for x^ = Q1 W2^{-1} F,
+      // which is G1 C also for a first core that is not orthonormal
+      TT_TRY((gemm<float, float, float, float, false, false>(plan_gemm(r, r, M, false), G[par][0], r, G[par][0], r,
+                                                             fW2[par], r, 1, 0, nullptr, nullptr, nullptr, nullptr, s)));
+      TT_TRY((gemm<float, float, float, float, true, false>(plan_gemm(r, (int)J, r, false), fW2[par], r, C[par], J,
+                                                            fC[par], J, 1, 0, nullptr, nullptr, nullptr, nullptr, s)));
       fast::k_make_half_copy<TX><<<1, 1024, 0, s>>>(fC[par], r * J, fCh[par], fShift + par,
                                                     std::is_same<TX, __half>::value ? 1 : 0);
       TT_CUDA(cudaGetLastError());
@@ -1046,8 +1092,9 @@ const char* ttals_status_string(ttals_status st) {
 
 const char* ttals_last_error(void) { return g_last_err.c_str(); }
 
-ttals_status ttals_create(int n_slice_modes, const int64_t* dims, const int64_t* ranks, const ttals_config* cfg,
-                          ttals_stream** out) {
+// one stream (nbatch = 1) or a batch of nbatch streams of one shape that share launches
+static ttals_status create_streams(int nbatch, int n_slice_modes, const int64_t* dims, const int64_t* ranks,
+                                   const ttals_config* cfg, ttals_stream** out) {
   if (!out) return TTALS_EINVAL;
   *out = nullptr;
   if (n_slice_modes < 2 || n_slice_modes > kMaxLevels || !dims || !ranks) return TTALS_EINVAL;
@@ -1110,27 +1157,37 @@ ttals_status ttals_create(int n_slice_modes, const int64_t* dims, const int64_t*
   s->ingest = c.ingest;
   s->device = c.device;
   s->qr_passes = c.qr_passes ? c.qr_passes : 2;
+  s->nbatch = nbatch;
   if (cudaEventCreateWithFlags(&s->ev, cudaEventDisableTiming) != cudaSuccess) {
     delete s;
     return TTALS_ECUDA;
   }
   ttals_status st = s->allocate();
+  if (st == TTALS_OK && nbatch > 1 && !s->batch_capable()) {
+    g_last_err = "batches need the fused path: FP16/BF16 ingest, a saturated second level, r_1 <= 64, "
+                 "I_2...I_{n-1} a multiple of 8";
+    st = TTALS_EINVAL;
+  }
   if (st != TTALS_OK) {
     delete s;
     return st;
   }
-  // default initial cores: Gaussian (SplitMix64 + Box-Muller)
+  // default initial cores: Gaussian (SplitMix64 + Box-Muller), one draw per stream of a batch
   SplitMix64 rng{c.seed};
   std::vector<std::vector<double>> cores(m);
   std::vector<const double*> ptrs(m);
-  for (int k = 1; k <= m; ++k) {
-    cores[k - 1].resize((size_t)s->core_elems(k));
-    for (double& v : cores[k - 1]) v = rng.gauss();
-    ptrs[k - 1] = cores[k - 1].data();
-  }
   std::vector<double> g((size_t)s->full[m]);
-  for (double& v : g) v = rng.gauss();
-  st = s->set_cores(ptrs.data(), g.data(), 0);
+  for (int b = 0; b < nbatch && st == TTALS_OK; ++b) {
+    for (int k = 1; k <= m; ++k) {
+      cores[k - 1].resize((size_t)s->core_elems(k));
+      for (double& v : cores[k - 1]) v = rng.gauss();
+      ptrs[k - 1] = cores[k - 1].data();
+    }
+    for (double& v : g) v = rng.gauss();
+    st = s->select_slot(b);
+    if (st == TTALS_OK) st = s->set_cores(ptrs.data(), g.data(), 0);
+  }
+  if (st == TTALS_OK) st = s->select_slot(0);
   if (st != TTALS_OK) {
     delete s;
     return st;
@@ -1138,6 +1195,37 @@ ttals_status ttals_create(int n_slice_modes, const int64_t* dims, const int64_t*
   *out = s;
   return TTALS_OK;
 }
+
+ttals_status ttals_create(int n_slice_modes, const int64_t* dims, const int64_t* ranks, const ttals_config* cfg,
+                          ttals_stream** out) {
+  return create_streams(1, n_slice_modes, dims, ranks, cfg, out);
+}
+
+ttals_status ttals_create_batch(int n_streams, int n_slice_modes, const int64_t* dims, const int64_t* ranks,
+                                const ttals_config* cfg, ttals_stream** out) {
+  if (out) *out = nullptr;
+  if (n_streams < 1 || n_streams > TTALS_MAX_BATCH) return TTALS_EINVAL;
+  return create_streams(n_streams, n_slice_modes, dims, ranks, cfg, out);
+}
+
+ttals_status ttals_push_batch(ttals_stream* s, const void* slices_dev, ttals_dtype dtype, void* cuda_stream) {
+  if (!s || !slices_dev) return TTALS_EINVAL;
+  if (dtype != s->ingest) return TTALS_EINVAL;
+  if (((uintptr_t)slices_dev & 15u) != 0) return TTALS_EINVAL;
+  TT_TRY(set_device(s->device));
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  TT_TRY(s->order_after_last(st));
+  return s->push(slices_dev, st);
+}
+
+ttals_status ttals_batch_select(ttals_stream* s, int index) {
+  if (!s || index < 0 || index >= s->nbatch) return TTALS_EINVAL;
+  TT_TRY(set_device(s->device));
+  if (s->have_last) TT_CUDA(cudaStreamSynchronize(s->last));
+  return s->select_slot(index);
+}
+
+int ttals_batch_size(const ttals_stream* s) { return s ? s->nbatch : 0; }
 
 void ttals_destroy(ttals_stream* s) {
   if (!s) return;
@@ -1161,6 +1249,7 @@ ttals_status ttals_set_cores(ttals_stream* s, const double* const* cores, const 
 
 ttals_status ttals_push_slice(ttals_stream* s, const void* slice_dev, ttals_dtype dtype, void* cuda_stream) {
   if (!s || !slice_dev) return TTALS_EINVAL;
+  if (s->nbatch != 1) return TTALS_ESTATE;          // a batch steps through ttals_push_batch
   if (dtype != s->ingest) return TTALS_EINVAL;
   if (((uintptr_t)slice_dev & 15u) != 0) return TTALS_EINVAL;
   TT_TRY(set_device(s->device));

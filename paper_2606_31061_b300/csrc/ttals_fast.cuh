@@ -233,12 +233,12 @@ __device__ __forceinline__ float dsmem_sum8(uint32_t local_addr, int n) {
   return s;
 }
 
-// 2-D tensor copy (TMA) global -> shared, box at element coordinates (x inner, y outer)
-__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t bar) {
+// 3-D tensor copy (TMA) global -> shared: box at element coordinates (x inner, y, z outer)
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, int x, int y, int z, uint32_t bar) {
   asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];\n" ::"r"(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];\n" ::"r"(
           dst),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(bar)
       : "memory");
 }
 // byte offset of 16-byte chunk c of row `row` in a 128B-swizzled box (1024-byte aligned)
@@ -277,7 +277,13 @@ __host__ __device__ constexpr size_t k1_smem_bytes() {
 
 template <typename TX, int NP>
 __global__ void __launch_bounds__(K1_THREADS, 2)
-    k_fast_solve(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmB, SolveArgs a) {
+    k_fast_solve(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmB, SolveArgs a0) {
+  // stream blockIdx.z of a batch: its slice and its B are plane z of the 3-D maps
+  const int zs = blockIdx.z;
+  SolveArgs a = a0;
+  a.Y += (size_t)zs * a.M * a.r;
+  a.xx_part += (size_t)zs * gridDim.x * gridDim.y;
+  a.ctl += zs;
   static_assert(NP % 16 == 0 && NP >= 16 && NP <= 64, "NP");
   constexpr int NT = NP / 16;  // n8-tiles per warp (each warp covers NP/2 columns)
   constexpr uint32_t ABYTES = K1_BM * 128, BBYTES = NP * 128;
@@ -315,7 +321,7 @@ __global__ void __launch_bounds__(K1_THREADS, 2)
     for (int t = 0; t < K1_STAGES && t < ntk; ++t) {
       const uint32_t bar = smem_u32(&bars[t]);
       mbar_arrive_expect_tx(bar, ABYTES);
-      tma_load_2d(stageA(t), &tmX, (int)(kbeg + (long long)t * K1_BK), m0, bar);
+      tma_load_3d(stageA(t), &tmX, (int)(kbeg + (long long)t * K1_BK), m0, zs, bar);
     }
   }
   pdl_wait();       // the previous step's env kernel wrote B and ctl
@@ -328,7 +334,7 @@ __global__ void __launch_bounds__(K1_THREADS, 2)
         mbar_arrive_expect_tx(bar, 0);
       } else {
         mbar_arrive_expect_tx(bar, BBYTES);
-        tma_load_2d(stageB(t), &tmB, (int)(kbeg + (long long)t * K1_BK), 0, bar);
+        tma_load_3d(stageB(t), &tmB, (int)(kbeg + (long long)t * K1_BK), 0, zs, bar);
       }
     }
   }
@@ -388,12 +394,12 @@ __global__ void __launch_bounds__(K1_THREADS, 2)
       const int tn = t + K1_STAGES;
       const uint32_t bar = smem_u32(&bars[st]);
       mbar_arrive_expect_tx(bar, ABYTES);
-      tma_load_2d(stageA(st), &tmX, (int)(kbeg + (long long)tn * K1_BK), m0, bar);
+      tma_load_3d(stageA(st), &tmX, (int)(kbeg + (long long)tn * K1_BK), m0, zs, bar);
       if (bzero) {
         mbar_arrive_expect_tx(bar, 0);
       } else {
         mbar_arrive_expect_tx(bar, BBYTES);
-        tma_load_2d(stageB(st), &tmB, (int)(kbeg + (long long)tn * K1_BK), 0, bar);
+        tma_load_3d(stageB(st), &tmB, (int)(kbeg + (long long)tn * K1_BK), 0, zs, bar);
       }
     }
   }
@@ -482,7 +488,18 @@ __host__ __device__ constexpr size_t k1b_smem_bytes(int M, int r, int np) {
 }
 
 template <typename TX, int NP>
-__global__ void __launch_bounds__(K1B_THREADS, 1) k_fast_factor(FactorArgs a) {
+__global__ void __launch_bounds__(K1B_THREADS, 1) k_fast_factor(FactorArgs a0) {
+  // stream blockIdx.z of a batch: its state and scratch slabs
+  const int zs = blockIdx.z;
+  FactorArgs a = a0;
+  a.Y += (size_t)zs * a.M * a.r;
+  a.xx_part += (size_t)zs * a.nxx;
+  a.Qh = (void*)((TX*)a.Qh + (size_t)zs * a.M * NP);
+  a.Qst += (size_t)zs * a.M * a.r;
+  a.W2part += (size_t)zs * KB_CLUSTER * NP * NP;
+  a.hh_work += (size_t)zs * 2 * a.M * a.r;
+  a.Qfb += (size_t)zs * a.M * a.r;
+  a.ctl += zs;
   extern __shared__ __align__(16) unsigned char smem[];
   constexpr int LDY = NP + 4, LQ = NP + 8, LDT = NP + 4;
   constexpr int NB = NP / 4, NBLK = NB * NB, NRG = k1b_rgroups(NP);
@@ -952,9 +969,35 @@ constexpr size_t k2_smem_bytes(int rch, int r) {
          (size_t)K2_BN * (r + 1) * 4 + (size_t)2 * NP * NP * 4 + 64;
 }
 
+// the environment kernels' arguments for stream z of a batch: its state slabs, its cc
+// partials and its ticket counter
+template <typename TX, int NP>
+__device__ __forceinline__ EnvArgs env_args_for_stream(const EnvArgs& a0, int z, int ncta_per_stream) {
+  EnvArgs a = a0;
+  const size_t mr = (size_t)a.M * a.r, rj = (size_t)a.r * a.J, rr = (size_t)a.r * a.r;
+  a.Qh = (const void*)((const TX*)a.Qh + (size_t)z * a.M * NP);
+  a.W2part += (size_t)z * KB_CLUSTER * NP * NP;
+  a.Cst += z * rj;
+  a.Chst = (void*)((TX*)a.Chst + z * rj);
+  a.ch_shift += 2 * z;
+  a.cc_part += (size_t)z * ncta_per_stream;
+  a.counter += 2 * z;
+  a.ctl += z;
+  a.Qst += z * mr;
+  a.W2st += z * rr;
+  a.Qold += z * mr;
+  a.Cold += z * rj;
+  a.Chold = (const void*)((const TX*)a.Chold + z * rj);
+  a.W2old += z * rr;
+  a.ch_shift_old += 2 * z;
+  return a;
+}
+
 template <typename TX, int NP>
 __global__ void __launch_bounds__(K2_THREADS, 2)
-    k_fast_env(const __grid_constant__ CUtensorMap tmX, EnvArgs a) {
+    k_fast_env(const __grid_constant__ CUtensorMap tmX, EnvArgs a0) {
+  const int zs = blockIdx.z;
+  const EnvArgs a = env_args_for_stream<TX, NP>(a0, zs, gridDim.x * gridDim.y);
   constexpr int NT = NP / 8;   // n8-tiles per warp (each warp covers all NP columns)
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
@@ -989,8 +1032,8 @@ __global__ void __launch_bounds__(K2_THREADS, 2)
     timeout_flag = 0;
     const uint32_t bar = smem_u32(&xbar);
     mbar_arrive_expect_tx(bar, (uint32_t)rch * 256);
-    tma_load_2d(xsub0, &tmX, (int)j0, i0, bar);
-    tma_load_2d(xsub1, &tmX, (int)j0 + 64, i0, bar);
+    tma_load_3d(xsub0, &tmX, (int)j0, i0, zs, bar);
+    tma_load_3d(xsub1, &tmX, (int)j0 + 64, i0, zs, bar);
   }
   if (tr0) TTRACE(20);
   // 2. wait for the factor kernel (Q1, Nx, ctl)
@@ -1197,7 +1240,9 @@ __host__ __device__ constexpr bool k2s_fits(int M, int r) {
 
 template <typename TX, int NP>
 __global__ void __launch_bounds__(K2_THREADS, 1)
-    k_fast_env1(const __grid_constant__ CUtensorMap tmX, EnvArgs a) {
+    k_fast_env1(const __grid_constant__ CUtensorMap tmX, EnvArgs a0) {
+  const int zs = blockIdx.z;
+  const EnvArgs a = env_args_for_stream<TX, NP>(a0, zs, gridDim.x * gridDim.y);
   constexpr int NT = NP / 8;          // n8-tiles of the output per warp
   constexpr int MT = K2S_BN / 16;     // m16-tiles (64 columns)
   extern __shared__ unsigned char smem_raw[];
@@ -1234,7 +1279,7 @@ __global__ void __launch_bounds__(K2_THREADS, 1)
     timeout_flag = 0;
     const uint32_t bar = smem_u32(&xbar);
     mbar_arrive_expect_tx(bar, (uint32_t)NBX * RB * 128);
-    for (int b = 0; b < NBX; ++b) tma_load_2d(xs + (uint32_t)b * RB * 128, &tmX, (int)j0, b * RB, bar);
+    for (int b = 0; b < NBX; ++b) tma_load_3d(xs + (uint32_t)b * RB * 128, &tmX, (int)j0, b * RB, zs, bar);
   }
   if (tr0) TTRACE(20);
   // 2. wait for the factor kernel (Q1, Nx, ctl)

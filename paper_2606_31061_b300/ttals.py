@@ -24,7 +24,8 @@ EXPORTS = ("ttals_create", "ttals_destroy", "ttals_effective_ranks", "ttals_set_
            "ttals_push_slice", "ttals_reconstruct", "ttals_cores", "ttals_stats", "ttals_step",
            "ttals_sync", "ttals_device_bytes", "ttals_status_string", "ttals_last_error",
            "ttals_launch_count", "ttals_stats_async", "ttals_profile", "ttals_profile_read",
-           "ttals_slice_error_noalloc")
+           "ttals_slice_error_noalloc", "ttals_create_batch", "ttals_push_batch", "ttals_batch_select",
+           "ttals_batch_size")
 
 
 class TTALSError(RuntimeError):
@@ -70,6 +71,10 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "ttals_profile": (ctypes.c_int, [VP, ctypes.c_int]),
         "ttals_profile_read": (ctypes.c_int, [VP, P(ctypes.c_double), I64P]),
         "ttals_slice_error_noalloc": (ctypes.c_int, [VP, ctypes.c_int, VP, ctypes.c_int, ctypes.c_int64, VP, VP]),
+        "ttals_create_batch": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, I64P, I64P, P(Config), P(VP)]),
+        "ttals_push_batch": (ctypes.c_int, [VP, VP, ctypes.c_int, VP]),
+        "ttals_batch_select": (ctypes.c_int, [VP, ctypes.c_int]),
+        "ttals_batch_size": (ctypes.c_int, [VP]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -99,18 +104,27 @@ def _stream_handle(stream) -> Optional[int]:
 
 
 class Stream:
-    """One Online TT-ALS stream (a ttals_stream handle)."""
+    """One Online TT-ALS stream (a ttals_stream handle), or with n_streams > 0 a batch of that
+    many streams of one shape (ttals_create_batch) that step together (push_batch); the
+    per-stream methods then refer to the stream chosen by select()."""
 
     def __init__(self, dims: Sequence[int], ranks: Sequence[int], ingest: str = "f64",
-                 seed: int = 0x5EED, device: int = 0, qr_passes: int = 0):
+                 seed: int = 0x5EED, device: int = 0, qr_passes: int = 0, n_streams: int = 0):
         lib = load()
         self.dims = tuple(int(d) for d in dims)
         self.ingest = ingest
         cfg = Config(DTYPES[ingest], seed, device, qr_passes, (ctypes.c_int * 4)(0, 0, 0, 0))
         h = ctypes.c_void_p()
-        _check(lib.ttals_create(len(self.dims), _i64(self.dims), _i64(ranks), ctypes.byref(cfg),
-                                ctypes.byref(h)), "ttals_create")
+        if n_streams > 0:
+            code = lib.ttals_create_batch(int(n_streams), len(self.dims), _i64(self.dims), _i64(ranks),
+                                          ctypes.byref(cfg), ctypes.byref(h))
+            if code != 0:
+                raise TTALSError(code, "ttals_create_batch", lib.ttals_last_error().decode())
+        else:
+            _check(lib.ttals_create(len(self.dims), _i64(self.dims), _i64(ranks), ctypes.byref(cfg),
+                                    ctypes.byref(h)), "ttals_create")
         self._h = h
+        self.n_streams = int(lib.ttals_batch_size(h))
         out = (ctypes.c_int64 * len(self.dims))()
         _check(lib.ttals_effective_ranks(h, out), "ttals_effective_ranks")
         self.ranks = tuple(int(v) for v in out)
@@ -201,6 +215,19 @@ class Stream:
     def stats_async(self, out_ptr: int, stream=None):
         _check(load().ttals_stats_async(self._h, ctypes.c_void_p(out_ptr),
                                         ctypes.c_void_p(_stream_handle(stream))), "ttals_stats_async")
+
+    def push_batch(self, slices, stream=None):
+        """ttals_push_batch: one step of every stream; `slices` is a contiguous CUDA tensor of
+        n_streams slices (stream b's slice is slices[b])."""
+        self.push_batch_ptr(slices.data_ptr(), _stream_handle(stream))
+
+    def push_batch_ptr(self, ptr: int, stream_handle: int):
+        _check(load().ttals_push_batch(self._h, ctypes.c_void_p(ptr), DTYPES[self.ingest],
+                                       ctypes.c_void_p(stream_handle)), "ttals_push_batch")
+
+    def select(self, index: int):
+        """ttals_batch_select: later per-stream calls refer to stream `index` of the batch."""
+        _check(load().ttals_batch_select(self._h, int(index)), "ttals_batch_select")
 
     def profile(self, enable: bool):
         _check(load().ttals_profile(self._h, 1 if enable else 0), "ttals_profile")

@@ -55,6 +55,14 @@ def test_invalid_arguments_rejected_before_cuda(lib):
     assert lib.ttals_push_slice(None, None, 0, None) == 1
     assert lib.ttals_sync(None) == 1
     assert lib.ttals_device_bytes(None) == 0
+    dims = (ctypes.c_int64 * 2)(64, 64)
+    ranks = (ctypes.c_int64 * 2)(8, 8)
+    assert lib.ttals_create_batch(0, 2, dims, ranks, None, ctypes.byref(h)) == 1      # no streams
+    assert lib.ttals_create_batch(65, 2, dims, ranks, None, ctypes.byref(h)) == 1     # above TTALS_MAX_BATCH
+    assert not h.value
+    assert lib.ttals_push_batch(None, None, 0, None) == 1
+    assert lib.ttals_batch_select(None, 0) == 1
+    assert lib.ttals_batch_size(None) == 0
 
 
 def test_no_device_fails_loudly(lib):
