@@ -299,7 +299,10 @@ struct Impl final : ttals_stream {
   float* fW2part = nullptr;     // [8][NP*NP] W2 partials of the factor kernel's ranks
   float* fQfb = nullptr;
   float2* fCC = nullptr;       // float-float partials of ||x^||^2 (env CTAs)
-  bool k2_single = false;       // environment kernel: one CTA per 64-column tile over all rows
+  // environment kernel: clustered row chunks, one CTA per 64-column tile over all rows, or
+  // 64-column tiles with the rows streamed through a pipeline
+  enum { K2_CLUSTER = 0, K2_SINGLE = 1, K2_STREAM = 2 };
+  int k2_kind = K2_CLUSTER;
   unsigned* fCounter = nullptr; // [nbatch][2]
   CUtensorMap mapB[2];          // TMA maps of fChb[p] (nbatch x r x rest_1, box 64 x NP)
 
@@ -371,8 +374,11 @@ struct Impl final : ttals_stream {
     if constexpr (kHalfIngest) {
       TT_CUDA(cudaFuncSetAttribute(fast::k_fast_solve<TX, NP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    (int)k1_smem));
-      if (k2_single)
+      if (k2_kind == K2_SINGLE)
         TT_CUDA(cudaFuncSetAttribute(fast::k_fast_env1<TX, NP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)k2_smem));
+      else if (k2_kind == K2_STREAM)
+        TT_CUDA(cudaFuncSetAttribute(fast::k_fast_env_stream<TX, NP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)k2_smem));
       else
         TT_CUDA(cudaFuncSetAttribute(fast::k_fast_env<TX, NP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -397,8 +403,10 @@ struct Impl final : ttals_stream {
       return TTALS_OK;
     }
     k1_rows = (int)cdiv(M, fast::K1_BM);
+    // k-splits of the solve: enough CTAs for two per SM over the whole batch, and no more
+    // (a batch fills the GPU with row tiles; fewer splits mean longer, cheaper CTAs)
     k1_split = 8;
-    while (k1_split > 1 && (long long)k1_rows * k1_split > 2 * kSMs) k1_split >>= 1;
+    while (k1_split > 1 && (long long)k1_rows * k1_split * nbatch > 2 * kSMs) k1_split >>= 1;
     k1_kchunk = cdiv(cdiv(J, k1_split), fast::K1_BK) * fast::K1_BK;
     k2_cols = (int)cdiv(J, fast::K2_BN);
     // row chunks per cluster: the fewest (largest chunks) that keep two env CTAs per SM
@@ -430,12 +438,31 @@ struct Impl final : ttals_stream {
         case 64: fits = fast::k2s_fits<64>((int)M, r); b1 = fast::k2s_smem_bytes<64>((int)M, r); break;
         default: break;
       }
-      if (fits && std::getenv("TTALS_ENV_CLUSTER") == nullptr) {
-        k2_single = true;
+      // environment kernel: streamed row stages for batches (many column tiles, several CTAs
+      // per SM); for one stream the whole-column CTA when its tile fits, else the cluster
+      // kernel.  TTALS_ENV_KERNEL=cluster|single|stream overrides (single only if it fits).
+      k2_kind = nbatch > 1 ? K2_STREAM : (fits ? K2_SINGLE : K2_CLUSTER);
+      if (const char* e = std::getenv("TTALS_ENV_KERNEL")) {
+        const std::string v(e);
+        if (v == "cluster") k2_kind = K2_CLUSTER;
+        else if (v == "stream") k2_kind = K2_STREAM;
+        else if (v == "single" && fits) k2_kind = K2_SINGLE;
+      }
+      if (k2_kind == K2_SINGLE) {
         k2_nq = 1;
         k2_cols = (int)cdiv(J, fast::K2S_BN);
         k2_rch = fast::k2s_box_rows((int)M);      // TMA box height of the env kernel's X map
         k2_smem = b1;
+      } else if (k2_kind == K2_STREAM) {
+        k2_nq = 1;
+        k2_cols = (int)cdiv(J, fast::K2S_BN);
+        k2_rch = fast::K1_BM;                     // reads X through the solve kernel's map
+        switch (np_) {
+          case 16: k2_smem = fast::k2p_smem_bytes<16>(); break;
+          case 32: k2_smem = fast::k2p_smem_bytes<32>(); break;
+          case 48: k2_smem = fast::k2p_smem_bytes<48>(); break;
+          default: k2_smem = fast::k2p_smem_bytes<64>(); break;
+        }
       }
     }
     switch (np_) {
@@ -617,10 +644,14 @@ struct Impl final : ttals_stream {
       c2.blockDim = dim3(fast::K2_THREADS, 1, 1);
       c2.dynamicSmemBytes = k2_smem;
       c2.stream = s;
-      if (k2_single) {
+      if (k2_kind == K2_SINGLE) {
         c2.attrs = at + 1;       // no cluster
         c2.numAttrs = 1;
         TT_CUDA(cudaLaunchKernelEx(&c2, fast::k_fast_env1<TX, NP>, mapX2, a2));
+      } else if (k2_kind == K2_STREAM) {
+        c2.attrs = at + 1;       // no cluster
+        c2.numAttrs = 1;
+        TT_CUDA(cudaLaunchKernelEx(&c2, fast::k_fast_env_stream<TX, NP>, mapX1, a2));
       } else {
         c2.attrs = at;
         c2.numAttrs = 2;

@@ -1425,6 +1425,246 @@ __global__ void __launch_bounds__(K2_THREADS, 1)
   TTRACE(28);
 }
 
+// ================================================================ K2 (streamed row stages)
+// F^T = X_(1)^T Q1 for a 64-column tile of X, the I_1 rows streamed through a pipeline of
+// 64-row stages: X by TMA (the solve kernel's 64 x 64 boxes; the first stages are requested
+// before the dependency wait), Q1 rows by cp.async into an XOR-swizzled layout.  The 8 warps
+// split the 64 x NP output tile (warp w: columns 16 (w % 4).., n8-tiles of half w / 4) and each
+// accumulates over all rows in row order, so no cross-warp reduction is needed.  Small shared
+// memory (two or more CTAs per SM) and long row loops: the kernel for batches of streams,
+// whose grids hold many column tiles.
+constexpr int K2P_BM = 64;            // rows of X per stage
+template <int NP>
+__host__ __device__ constexpr int k2p_stages() { return NP <= 32 ? 6 : 4; }
+// bytes per Q1 row in a stage: NP 16-bit values, rows of 48 padded to 64 (128 B)
+template <int NP>
+__host__ __device__ constexpr int k2p_qrow() { return NP == 48 ? 128 : NP * 2; }
+// byte offset of 16-byte chunk c of row `row` in a Q1 stage (conflict-free ldmatrix)
+template <int NP>
+__device__ __forceinline__ uint32_t k2p_qaddr(int row, int c) {
+  if constexpr (NP == 48) return swz(row, c);
+  else return qswz<NP>(row, c);
+}
+template <int NP>
+__host__ __device__ constexpr size_t k2p_smem_bytes() {
+  // X stages (64 x 128 B, 128B-swizzled) | Q1 stages (64 rows) | Nx, D2 (NP x NP each);
+  // my columns of F (64 x (r+1) floats) reuse the X stages after the loop
+  return 1024 + (size_t)k2p_stages<NP>() * (K2P_BM * 128 + K2P_BM * k2p_qrow<NP>()) + (size_t)2 * NP * NP * 4;
+}
+
+template <typename TX, int NP>
+__global__ void __launch_bounds__(K2_THREADS, 2)
+    k_fast_env_stream(const __grid_constant__ CUtensorMap tmX, EnvArgs a0) {
+  const int zs = blockIdx.z;
+  const EnvArgs a = env_args_for_stream<TX, NP>(a0, zs, gridDim.x * gridDim.y);
+  constexpr int ST = k2p_stages<NP>();
+  constexpr int NT8 = NP / 8;         // n8-tiles of the output tile
+  constexpr int NTW = NT8 / 2;        // n8-tiles per warp
+  constexpr int CPR = NP / 8;         // 16-byte chunks per Q1 row
+  constexpr uint32_t XB = K2P_BM * 128, QB = K2P_BM * k2p_qrow<NP>();
+  static_assert(K2S_BN == 64 && K2_THREADS == 256, "warp tiling assumes 64 columns and 8 warps");
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+  const int M = a.M, r = a.r, rr = r * r;
+  const uint32_t xs = smem_u32(smem);                          // X stage s at xs + s*XB
+  const uint32_t qs = xs + ST * XB;                            // Q1 stage s at qs + s*QB
+  float* sN = reinterpret_cast<float*>(smem + ST * (XB + QB)); // Nx, NP x NP, zero past r
+  float* sW = sN + NP * NP;                                    // D2 = W2 - I (NP x NP)
+  const int LDF = r + 1;
+  float* sF = reinterpret_cast<float*>(smem);                  // [64][r+1] after the loop
+  __shared__ __align__(8) uint64_t bars[ST];
+  __shared__ float redf[64];
+  __shared__ int last_flag;
+  __shared__ int timeout_flag;
+
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int ct = blockIdx.x;
+  const long long j0 = (long long)ct * K2S_BN;
+  const int xcols = (a.J - j0 < K2S_BN) ? (int)(a.J - j0) : K2S_BN;
+  const int nt = (M + K2P_BM - 1) / K2P_BM;
+  const bool tr0 = (blockIdx.x == 0);
+  const bool W2_WRITER = (blockIdx.x == 0);   // one CTA writes the state's W2
+
+  // 1. the first X stages (independent of the previous kernels)
+  if (tid == 0) {
+    asm volatile("prefetch.tensormap [%0];\n" ::"l"(reinterpret_cast<uint64_t>(&tmX)) : "memory");
+    for (int st = 0; st < ST; ++st) mbar_init(smem_u32(&bars[st]), 1);
+    mbar_fence_init();
+    timeout_flag = 0;
+    for (int st = 0; st < ST && st < nt; ++st) {
+      const uint32_t bar = smem_u32(&bars[st]);
+      mbar_arrive_expect_tx(bar, XB);
+      tma_load_3d(xs + st * XB, &tmX, (int)j0, st * K2P_BM, zs, bar);
+    }
+  }
+  __syncthreads();
+  if (tr0) TTRACE(20);
+  // 2. wait for the factor kernel (Q1, W2 partials, ctl)
+  pdl_wait();
+  pdl_trigger();
+  if (tr0) TTRACE(21);
+  const double xx = a.ctl->xx;     // ||x||^2 of this slice (factor kernel)
+  double sum_xx = 0.0, sum_ee = 0.0;
+  long long tcount = 0;
+  if (tid == 0) {
+    sum_xx = a.ctl->sum_xx;
+    sum_ee = a.ctl->sum_ee;
+    tcount = a.ctl->t;
+  }
+  if (a.ctl->skip) {
+    // non-finite slice: the new state is the old one
+    const long long nthr = (long long)gridDim.x * K2_THREADS;
+    const long long me = (long long)blockIdx.x * K2_THREADS + tid;
+    for (long long e = me; e < (long long)M * r; e += nthr) a.Qst[e] = a.Qold[e];
+    for (long long e = me; e < (long long)r * a.J; e += nthr) {
+      a.Cst[e] = a.Cold[e];
+      ((TX*)a.Chst)[e] = ((const TX*)a.Chold)[e];
+    }
+    for (long long e = me; e < rr; e += nthr) a.W2st[e] = a.W2old[e];
+    if (me == 0) *a.ch_shift = *a.ch_shift_old;
+    bool ok = true;
+    for (int st = 0; st < ST && st < nt; ++st) ok = mbar_wait(smem_u32(&bars[st]), 0) && ok;
+    if (!ok && tid == 0) a.ctl->latched = 5;
+    return;
+  }
+  // Q1 rows [64 t, 64 t + 64) into Q stage t % ST (rows past I_1 zero)
+  const TX* Qh = (const TX*)a.Qh;
+  auto load_q = [&](int t) {
+    const uint32_t dst = qs + (uint32_t)(t % ST) * QB;
+    for (int c = tid; c < K2P_BM * CPR; c += K2_THREADS) {
+      const int lr = c / CPR, ch = c % CPR;
+      const int row = t * K2P_BM + lr;
+      const bool ok = row < M;
+      cp_async16(dst + k2p_qaddr<NP>(lr, ch), Qh + (ok ? (long long)row * NP + ch * 8 : 0), ok ? 16u : 0u);
+    }
+  };
+  for (int t = 0; t < ST - 1; ++t) {
+    if (t < nt) load_q(t);
+    cp_async_commit();
+  }
+  env_w2_nx<NP>(a.W2part, r, sW, sN, a.W2st, W2_WRITER);
+  if (tr0) TTRACE(22);
+  // 3. F^T (64 x NP) = X^T Q1 over the row stages
+  const int wm = warp & 3, wn = (warp >> 2) * NTW;
+  float acc[NTW][4];
+#pragma unroll
+  for (int n = 0; n < NTW; ++n) acc[n][0] = acc[n][1] = acc[n][2] = acc[n][3] = 0.f;
+  int t_done = nt;
+  for (int t = 0; t < nt; ++t) {
+    const int st = t % ST;
+    if (t + ST - 1 < nt) load_q(t + ST - 1);     // its buffer was released at the end of t - 1
+    cp_async_commit();
+    cp_async_wait<ST - 1>();                     // this thread's copies of stage t landed
+    if (!mbar_wait(smem_u32(&bars[st]), (uint32_t)((t / ST) & 1))) timeout_flag = 1;
+    __syncthreads();
+    const uint32_t xst = xs + st * XB, qst = qs + st * QB;
+#pragma unroll
+    for (int k0 = 0; k0 < K2P_BM; k0 += 16) {
+      uint32_t af[4];
+      {
+        const int row = k0 + (lane & 7) + ((lane >> 4) << 3);
+        ldsm_x4_t(xst + swz(row, 2 * wm + ((lane >> 3) & 1)), af[0], af[1], af[2], af[3]);
+      }
+      const int qrow = k0 + (lane & 7) + (((lane >> 3) & 1) << 3);
+#pragma unroll
+      for (int p = 0; p < NTW / 2; ++p) {
+        uint32_t b0, b1, b2, b3;
+        ldsm_x4_t(qst + k2p_qaddr<NP>(qrow, wn + 2 * p + (lane >> 4)), b0, b1, b2, b3);
+        mma16816<TX>(acc[2 * p], af, b0, b1);
+        mma16816<TX>(acc[2 * p + 1], af, b2, b3);
+      }
+      if constexpr (NTW % 2 == 1) {
+        uint32_t b0, b1;
+        ldsm_x2_t(qst + k2p_qaddr<NP>(qrow, wn + NTW - 1), b0, b1);
+        mma16816<TX>(acc[NTW - 1], af, b0, b1);
+      }
+    }
+    __syncthreads();                             // every warp is done with stage st
+    if (timeout_flag) {                          // uniform (read after the barrier)
+      t_done = t + 1;
+      break;
+    }
+    if (tid == 0 && t + ST < nt) {
+      const uint32_t bar = smem_u32(&bars[st]);
+      mbar_arrive_expect_tx(bar, XB);
+      tma_load_3d(xst, &tmX, (int)j0, (t + ST) * K2P_BM, zs, bar);
+    }
+  }
+  cp_async_wait<0>();
+  if (t_done < nt) {
+    // a wait gave up: wait (bounded) for the X stages still in flight before the buffers are
+    // reused, then finish with the step marked failed (ETIMEOUT)
+    for (int t = t_done; t < nt && t < t_done + ST - 1; ++t)
+      mbar_wait(smem_u32(&bars[t % ST]), (uint32_t)((t / ST) & 1));
+    __syncthreads();
+  }
+  {
+    const int g = lane >> 2, t4 = lane & 3;
+#pragma unroll
+    for (int n = 0; n < NTW; ++n) {
+      const int c = (wn + n) * 8 + 2 * t4, jl = wm * 16 + g;
+      if (c < r) {
+        sF[jl * LDF + c] = acc[n][0];
+        sF[(jl + 8) * LDF + c] = acc[n][2];
+      }
+      if (c + 1 < r) {
+        sF[jl * LDF + c + 1] = acc[n][1];
+        sF[(jl + 8) * LDF + c + 1] = acc[n][3];
+      }
+    }
+  }
+  if (tid == 0 && timeout_flag) a.ctl->latched = 5;
+  __syncthreads();
+  if (tr0) TTRACE(23);
+  // 4. write F and its ingest-type copy (coalesced along j); ||x^||^2 of my columns
+  int shift = 0;
+  if (a.is_half && xx > 0.0) {
+    const float nrm = sqrtf((float)xx);
+    shift = nrm > 16384.f ? (int)ceilf(log2f(nrm / 16384.f)) : 0;
+  }
+  if (ct == 0 && tid == 0) *a.ch_shift = shift;
+  const float scale = ldexpf(1.0f, -shift);
+  float ph = 0.f, pl = 0.f;     // float-float partial of ||x^||^2
+  env_columns_out<TX, NP>(sF, LDF, sN, xcols, r, a.J, j0, a.Cst, (TX*)a.Chst, scale, ph, pl);
+  const float2 cc_cta = ff_block_sum(ph, pl, redf);
+  if (tr0) TTRACE(24);
+  // one partial per CTA; the last CTA of the stream's grid sums them in a fixed order
+  const int ncta = (int)gridDim.x;
+  if (tid == 0) {
+    a.cc_part[ct] = cc_cta;
+    __threadfence();
+    const unsigned done = atomicAdd(a.counter, 1u);
+    last_flag = (done == (unsigned)ncta - 1u);
+  }
+  __syncthreads();
+  if (!last_flag) return;
+  __threadfence();
+  float sh = 0.f, sl = 0.f;
+  for (int b0 = tid; b0 < ncta; b0 += 4 * K2_THREADS) {
+    float2 v[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+      v[u] = (b0 + u * K2_THREADS < ncta) ? __ldcg(a.cc_part + b0 + u * K2_THREADS) : make_float2(0.f, 0.f);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) ff_add(sh, sl, v[u].x, v[u].y);
+  }
+  const float2 ccf = ff_block_sum(sh, sl, redf);
+  if (tid == 0) {
+    const double cc = (double)ccf.x + (double)ccf.y;
+    *a.counter = 0u;
+    Ctl* c = a.ctl;
+    if (!isfinite(cc)) c->latched = 4;
+    const double ccv = isfinite(cc) ? cc : 0.0;
+    const double ee = xx - ccv > 0.0 ? xx - ccv : 0.0;
+    c->cc = ccv;
+    c->ee = ee;
+    c->sum_xx = sum_xx + xx;
+    c->sum_ee = sum_ee + ee;
+    c->t = tcount + 1;
+  }
+  TTRACE(28);
+}
+
 // ------------------------------------------------ helpers for the lazy finalisation
 // W2 (FP32, r x r) -> T = R2^{-1}, R2 = chol(W2) in FP64 (one CTA; output path only).
 __global__ void k_chol64_inverse(const float* __restrict__ W2, int r, double* __restrict__ T64,

@@ -1,6 +1,13 @@
-"""Batches of streams (ttals_create_batch / ttals_push_batch): every stream of a batch must
-give the same results as the same stream run alone, bit for bit (the same kernels and the
-same reduction orders; a batch only adds a stream index to each launch's grid)."""
+"""Batches of streams (ttals_create_batch / ttals_push_batch).
+
+* Alone vs in a batch: a batch runs the kernels tuned for throughput (rows streamed through
+  a pipeline in the environment kernel, fewer k-splits of the solve), a lone stream the ones
+  tuned for latency, so the two agree to FP32 summation order, not bitwise.  Checked per
+  stream: the relative reconstruction error (RE, Sec. 5.1) within 1e-3 absolute (the FP16
+  ingest bar against the FP64 oracle) and every reconstructed slice within 1e-3 relative.
+* In the mix: a stream's results do not depend on its slot or on the other streams' data,
+  bit for bit (same batch size, permuted slots, one stream replaced).
+"""
 import numpy as np
 import pytest
 
@@ -8,6 +15,9 @@ from oracle import ttals_oracle as O
 from paper_2606_31061_b300 import synth
 
 pytestmark = pytest.mark.gpu
+
+SHAPES = [("video", {"dims": (96, 128, 3)}), ("square", {"s": 128, "r": 16}), ("square", {"s": 192, "r": 40}),
+          ("square", {"s": 160, "r": 64})]
 
 
 def _torch():
@@ -17,17 +27,12 @@ def _torch():
     return torch
 
 
-def _streams(name, nb, T, **kw):
-    """nb independent streams of one shape: dims, ranks, FP16 payloads [b][t], cores[b], g[b]."""
-    frames, cores, gs = [], [], []
-    for b in range(nb):
-        sp = synth.make_stream(name, seed=5000 + 17 * b, **kw)
-        r = O.clamp_ranks(sp.dims, sp.ranks)
-        c, g = synth.init_cores(sp.dims, r, seed=300 + b)
-        frames.append([synth.round_to_ingest(x, "f16")[0] for x in sp.take(T)])
-        cores.append(c)
-        gs.append(g)
-    return sp.dims, sp.ranks, frames, cores, gs
+def _stream(name, kw, b, T):
+    """Stream number b of a shape: dims, ranks, FP16 payloads, initial cores and g."""
+    sp = synth.make_stream(name, seed=5000 + 17 * b, **kw)
+    r = O.clamp_ranks(sp.dims, sp.ranks)
+    c, g = synth.init_cores(sp.dims, r, seed=300 + b)
+    return sp.dims, sp.ranks, [synth.round_to_ingest(x, "f16")[0] for x in sp.take(T)], c, g
 
 
 def _run_alone(torch, dims, ranks, frames, cores, g):
@@ -45,32 +50,59 @@ def _run_alone(torch, dims, ranks, frames, cores, g):
     return xs, stats
 
 
-# video-shaped (env kernel: one CTA per column tile) and square r = 40 (rank padded to 48:
-# the clustered env kernel)
-@pytest.mark.parametrize("name,kw", [("video", {"dims": (96, 128, 3)}), ("square", {"s": 128, "r": 16}),
-                                     ("square", {"s": 192, "r": 40})])
-def test_batch_equals_alone_bitwise(name, kw):
-    torch = _torch()
+def _run_batch(torch, dims, ranks, streams):
+    """streams: list of (frames, cores, g); returns per stream (x^ list, stats list)."""
     from paper_2606_31061_b300.ttals import Stream
-    nb, T = 3, 4
-    dims, ranks, frames, cores, gs = _streams(name, nb, T, **kw)
-    alone = [_run_alone(torch, dims, ranks, frames[b], cores[b], gs[b]) for b in range(nb)]
+    nb, T = len(streams), len(streams[0][0])
     bt = Stream(dims, ranks, ingest="f16", n_streams=nb)
     assert bt.n_streams == nb
-    for b in range(nb):
+    for b, (_, c, g) in enumerate(streams):
         bt.select(b)
-        bt.set_cores(cores[b], gs[b])
+        bt.set_cores(c, g)
     out = torch.empty(tuple(dims), dtype=torch.float64, device="cuda")
+    res = [([], []) for _ in range(nb)]
     for t in range(T):
-        batch = torch.from_numpy(np.stack([frames[b][t] for b in range(nb)])).view(torch.float16).cuda()
+        batch = torch.from_numpy(np.stack([s[0][t] for s in streams])).view(torch.float16).cuda()
         bt.push_batch(batch)
         for b in range(nb):
             bt.select(b)
             bt.reconstruct(out, "f64")
-            x = out.cpu().numpy()
-            assert np.array_equal(x, alone[b][0][t]), (name, b, t, float(np.abs(x - alone[b][0][t]).max()))
-            assert np.array_equal(np.array(bt.stats()), alone[b][1][t]), (name, b, t)
+            res[b][0].append(out.cpu().numpy().copy())
+            res[b][1].append(np.array(bt.stats()))
     bt.close()
+    return res
+
+
+@pytest.mark.parametrize("name,kw", SHAPES)
+def test_batch_matches_alone(name, kw):
+    torch = _torch()
+    nb, T = 3, 5
+    ss = [_stream(name, kw, b, T) for b in range(nb)]
+    dims, ranks = ss[0][0], ss[0][1]
+    batch = _run_batch(torch, dims, ranks, [(s[2], s[3], s[4]) for s in ss])
+    for b, s in enumerate(ss):
+        xa, sa = _run_alone(torch, dims, ranks, s[2], s[3], s[4])
+        xb, sb = batch[b]
+        for t in range(T):
+            rel = np.linalg.norm(xb[t] - xa[t]) / max(np.linalg.norm(xa[t]), 1e-300)
+            assert rel <= 1e-3, (name, b, t, rel)
+        re_a = np.sqrt(sa[-1][3] / sa[-1][2])
+        re_b = np.sqrt(sb[-1][3] / sb[-1][2])
+        assert abs(re_a - re_b) <= 1e-3, (name, b, re_a, re_b)
+
+
+@pytest.mark.parametrize("name,kw", SHAPES[:2])
+def test_batch_slot_and_neighbours_bitwise(name, kw):
+    torch = _torch()
+    T = 4
+    s0, s1, s2, s3 = (_stream(name, kw, b, T) for b in range(4))
+    dims, ranks = s0[0], s0[1]
+    A = _run_batch(torch, dims, ranks, [(s[2], s[3], s[4]) for s in (s0, s1, s2)])
+    B = _run_batch(torch, dims, ranks, [(s[2], s[3], s[4]) for s in (s3, s0, s1)])
+    for a, b in ((0, 1), (1, 2)):
+        for t in range(T):
+            assert np.array_equal(A[a][0][t], B[b][0][t]), (name, a, t)
+            assert np.array_equal(A[a][1][t], B[b][1][t]), (name, a, t)
 
 
 def test_batch_argument_errors():
