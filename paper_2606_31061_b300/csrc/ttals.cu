@@ -455,7 +455,7 @@ struct Impl final : ttals_stream {
         k2_smem = b1;
       } else if (k2_kind == K2_STREAM) {
         k2_nq = 1;
-        k2_cols = (int)cdiv(J, fast::K2S_BN);
+        k2_cols = (int)cdiv(J, fast::K2P_BN);
         k2_rch = fast::K1_BM;                     // reads X through the solve kernel's map
         switch (np_) {
           case 16: k2_smem = fast::k2p_smem_bytes<16>(); break;
@@ -649,6 +649,7 @@ struct Impl final : ttals_stream {
         c2.numAttrs = 1;
         TT_CUDA(cudaLaunchKernelEx(&c2, fast::k_fast_env1<TX, NP>, mapX2, a2));
       } else if (k2_kind == K2_STREAM) {
+        c2.blockDim = dim3(fast::K2P_THREADS, 1, 1);
         c2.attrs = at + 1;       // no cluster
         c2.numAttrs = 1;
         TT_CUDA(cudaLaunchKernelEx(&c2, fast::k_fast_env_stream<TX, NP>, mapX1, a2));

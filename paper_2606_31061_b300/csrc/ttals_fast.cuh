@@ -250,29 +250,38 @@ __device__ __forceinline__ unsigned short tx_bits(__nv_bfloat16 v) { return __bf
 // ================================================================ K1: local solve
 // Y = X_(1) B^T for one 64-row tile of X and a k-split; the splits of a row tile form a
 // thread-block cluster and reduce their partial tiles through distributed shared memory
-// (fixed rank order).  Also per-cluster partials of ||x||^2 and of the Gram W1 = Y^T Y.
-// X and B arrive as 64 x 64 (resp. NP x 64) boxes through the TMA engine, 128B-swizzled,
-// out-of-range rows and columns zero-filled by the hardware.
-constexpr int K1_THREADS = 256;
+// (fixed rank order).  Also per-CTA partials of ||x||^2.
+// X and B arrive through the TMA engine in stages of two 64-column boxes (256 contiguous
+// bytes of every row per stage), 128B-swizzled, out-of-range rows and columns zero-filled by
+// the hardware.  Warp 8 issues the copies; warps 0-7 consume the stages and release each
+// one through its `empty` barrier, so no block-wide barrier sits in the main loop.
+constexpr int K1_CWARPS = 8;                        // consumer warps
+constexpr int K1_THREADS = (K1_CWARPS + 1) * 32;    // + the producer warp
 constexpr int K1_BM = 64;          // rows of X per CTA
-constexpr int K1_BK = 64;          // k per pipeline stage (128 bytes of a row)
-constexpr int K1_STAGES = 6;
+constexpr int K1_BK = 128;         // k per pipeline stage: two 64-column boxes
+constexpr int K1_MAXST = 4;
 
 struct SolveArgs {
   int M, r;
-  long long K, kchunk;    // kchunk % 64 == 0
+  long long K, kchunk;    // kchunk % K1_BK == 0
   float* Y;               // M x r
   float2* xx_part;        // [row tiles * splits] float-float partials of ||x||^2
   Ctl* ctl;
 };
 
 template <int NP>
+__host__ __device__ constexpr int k1_stages() { return NP <= 32 ? 4 : 3; }
+template <int NP>
 __host__ __device__ constexpr size_t k1_stage_bytes() {
-  return (size_t)(K1_BM + NP) * 128;
+  return (size_t)(K1_BM + NP) * 256;
 }
 template <int NP>
 __host__ __device__ constexpr size_t k1_smem_bytes() {
-  return (size_t)K1_STAGES * k1_stage_bytes<NP>() + 1024;   // + alignment slack
+  return (size_t)k1_stages<NP>() * k1_stage_bytes<NP>() + 1024;   // + alignment slack
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(bar) : "memory");
 }
 
 template <typename TX, int NP>
@@ -285,16 +294,20 @@ __global__ void __launch_bounds__(K1_THREADS, 2)
   a.xx_part += (size_t)zs * gridDim.x * gridDim.y;
   a.ctl += zs;
   static_assert(NP % 16 == 0 && NP >= 16 && NP <= 64, "NP");
+  constexpr int ST = k1_stages<NP>();
+  static_assert(ST <= K1_MAXST, "stages");
   constexpr int NT = NP / 16;  // n8-tiles per warp (each warp covers NP/2 columns)
-  constexpr uint32_t ABYTES = K1_BM * 128, BBYTES = NP * 128;
+  constexpr uint32_t ABOX = K1_BM * 128, BBOX = NP * 128;   // one 64-column box of X / of B
+  constexpr uint32_t ABYTES = 2 * ABOX, BBYTES = 2 * BBOX;
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
-  __shared__ __align__(8) uint64_t bars[K1_STAGES];
+  __shared__ __align__(8) uint64_t full[K1_MAXST];    // stage data landed (A arrival + B arrival)
+  __shared__ __align__(8) uint64_t empty[K1_MAXST];   // stage released by the 8 consumer warps
   __shared__ float redf[64];
   __shared__ int timeout_flag;
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int wr = warp & 3, wc = warp >> 2;
+  const int wr = warp & 3, wc = (warp >> 2) & 1;
   const uint32_t crank = cluster_rank();
   const int nsplit = gridDim.y;
   const int rt = blockIdx.x;
@@ -304,12 +317,26 @@ __global__ void __launch_bounds__(K1_THREADS, 2)
   const long long kend = (kbeg + a.kchunk < a.K) ? kbeg + a.kchunk : a.K;
   const int ntk = kend > kbeg ? (int)((kend - kbeg + K1_BK - 1) / K1_BK) : 0;
   const bool tr0 = (blockIdx.x == 0 && blockIdx.y == 0);
+  const bool producer = (warp == K1_CWARPS);
   const uint32_t sbase = smem_u32(smem);
   auto stageA = [&](int st) { return sbase + (uint32_t)(st * k1_stage_bytes<NP>()); };
   auto stageB = [&](int st) { return stageA(st) + ABYTES; };
+  auto load_a = [&](int t, int st) {
+    const int x = (int)(kbeg + (long long)t * K1_BK);
+    tma_load_3d(stageA(st), &tmX, x, m0, zs, smem_u32(&full[st]));
+    tma_load_3d(stageA(st) + ABOX, &tmX, x + 64, m0, zs, smem_u32(&full[st]));
+  };
+  auto load_b = [&](int t, int st) {
+    const int x = (int)(kbeg + (long long)t * K1_BK);
+    tma_load_3d(stageB(st), &tmB, x, 0, zs, smem_u32(&full[st]));
+    tma_load_3d(stageB(st) + BBOX, &tmB, x + 64, 0, zs, smem_u32(&full[st]));
+  };
 
   if (tid == 0) {
-    for (int s = 0; s < K1_STAGES; ++s) mbar_init(smem_u32(&bars[s]), 2);   // A arrival + B arrival
+    for (int s = 0; s < ST; ++s) {
+      mbar_init(smem_u32(&full[s]), 2);            // A arrival + B arrival
+      mbar_init(smem_u32(&empty[s]), K1_CWARPS);
+    }
     mbar_fence_init();
     timeout_flag = 0;
   }
@@ -317,30 +344,19 @@ __global__ void __launch_bounds__(K1_THREADS, 2)
   if (tr0) TTRACE(0);
   TTRACE_CTA(0);
   // A tiles do not depend on the previous kernel: start them before the dependency wait
-  if (tid == 0) {
-    for (int t = 0; t < K1_STAGES && t < ntk; ++t) {
-      const uint32_t bar = smem_u32(&bars[t]);
-      mbar_arrive_expect_tx(bar, ABYTES);
-      tma_load_3d(stageA(t), &tmX, (int)(kbeg + (long long)t * K1_BK), m0, zs, bar);
+  if (producer && lane == 0) {
+    for (int t = 0; t < ST && t < ntk; ++t) {
+      mbar_arrive_expect_tx(smem_u32(&full[t]), ABYTES);
+      load_a(t, t);
     }
   }
   pdl_wait();       // the previous step's env kernel wrote B and ctl
   pdl_trigger();    // the factor kernel may launch and wait for this grid
   const bool bzero = (a.ctl->cc == 0.0);
-  if (tid == 0) {
-    for (int t = 0; t < K1_STAGES && t < ntk; ++t) {
-      const uint32_t bar = smem_u32(&bars[t]);
-      if (bzero) {
-        mbar_arrive_expect_tx(bar, 0);
-      } else {
-        mbar_arrive_expect_tx(bar, BBYTES);
-        tma_load_3d(stageB(t), &tmB, (int)(kbeg + (long long)t * K1_BK), 0, zs, bar);
-      }
-    }
-  }
   if (bzero) {
-    // e_1 rule for a zero temporal row: the right part becomes e_0 e_0^T
-    for (int st = 0; st < K1_STAGES; ++st)
+    // e_1 rule for a zero temporal row: the right part becomes e_0 e_0^T (B stays zero, but
+    // for the one element of the first split's first stage)
+    for (int st = 0; st < ST; ++st)
       for (int e = tid; e < (int)BBYTES / 16; e += K1_THREADS)
         *reinterpret_cast<uint4*>(smem + (stageB(st) - sbase) + e * 16) = make_uint4(0, 0, 0, 0);
     __syncthreads();
@@ -352,69 +368,89 @@ __global__ void __launch_bounds__(K1_THREADS, 2)
 #pragma unroll
   for (int j = 0; j < NT; ++j) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.f;
   float ssh = 0.f, ssl = 0.f;    // ||x||^2 of the tiles seen by this thread (float-float)
-  int t_done = ntk;              // tiles consumed (fewer after a timed-out wait)
-  for (int t = 0; t < ntk; ++t) {
-    const int st = t % K1_STAGES;
-    if (!mbar_wait(smem_u32(&bars[st]), (uint32_t)((t / K1_STAGES) & 1))) timeout_flag = 1;
-    if (t == 0) TTRACE_CTA(1);
-    const uint32_t tA = stageA(st), tB = stageB(st);
-    float ss = 0.f;
-#pragma unroll
-    for (int kk = 0; kk < K1_BK / 16; ++kk) {
-      uint32_t af[4];
-      {
-        const int row = wr * 16 + (lane & 15);
-        ldsm_x4(tA + swz(row, kk * 2 + (lane >> 4)), af[0], af[1], af[2], af[3]);
+  if (producer) {
+    if (lane == 0) {
+      int issued = ntk < ST ? ntk : ST;
+      for (int t = 0; t < issued; ++t) {
+        if (bzero) {
+          mbar_arrive_expect_tx(smem_u32(&full[t]), 0);
+        } else {
+          mbar_arrive_expect_tx(smem_u32(&full[t]), BBYTES);
+          load_b(t, t);
+        }
       }
-      if (wc == 0) ss += frag_sumsq<TX>(af);
-#pragma unroll
-      for (int p = 0; p < NT / 2; ++p) {
-        uint32_t b0, b1, b2, b3;
-        const int n = wc * (NP / 2) + p * 16 + (lane & 7) + ((lane >> 4) << 3);
-        ldsm_x4(tB + swz(n, kk * 2 + ((lane >> 3) & 1)), b0, b1, b2, b3);
-        mma16816<TX>(acc[2 * p], af, b0, b1);
-        mma16816<TX>(acc[2 * p + 1], af, b2, b3);
+      for (int t = ST; t < ntk; ++t) {
+        const int st = t % ST;
+        if (!mbar_wait(smem_u32(&empty[st]), (uint32_t)(((t / ST) - 1) & 1)) || timeout_flag) {
+          timeout_flag = 1;
+          break;
+        }
+        if (t == ST && bzero && blockIdx.y == 0)
+          *reinterpret_cast<TX*>(smem + (stageB(0) - sbase)) = from_acc<TX>(0.f);
+        mbar_arrive_expect_tx(smem_u32(&full[st]), ABYTES);
+        load_a(t, st);
+        if (bzero) {
+          mbar_arrive_expect_tx(smem_u32(&full[st]), 0);
+        } else {
+          mbar_arrive_expect_tx(smem_u32(&full[st]), BBYTES);
+          load_b(t, st);
+        }
+        issued = t + 1;
       }
-      if constexpr (NT % 2 == 1) {
-        uint32_t b0, b1;
-        const int n = wc * (NP / 2) + (NT - 1) * 8 + (lane & 7);
-        ldsm_x2(tB + swz(n, kk * 2 + ((lane >> 3) & 1)), b0, b1);
-        mma16816<TX>(acc[NT - 1], af, b0, b1);
+      if (timeout_flag) {
+        // a wait gave up: wait (bounded) for the copies still in flight before the buffers
+        // are reused; the step is marked failed (ETIMEOUT)
+        for (int t = issued - ST > 0 ? issued - ST : 0; t < issued; ++t)
+          mbar_wait(smem_u32(&full[t % ST]), (uint32_t)((t / ST) & 1));
       }
     }
-    two_sum_acc(ssh, ssl, ss);
-    __syncthreads();          // every warp is done with stage st
-    if (timeout_flag) {       // uniform (read after the barrier): stop issuing, drain below
-      t_done = t + 1;
-      break;
-    }
-    if (t == 0 && bzero && blockIdx.y == 0 && tid == 0)
-      *reinterpret_cast<TX*>(smem + (stageB(0) - sbase)) = from_acc<TX>(0.f);
-    if (tid == 0 && t + K1_STAGES < ntk) {
-      const int tn = t + K1_STAGES;
-      const uint32_t bar = smem_u32(&bars[st]);
-      mbar_arrive_expect_tx(bar, ABYTES);
-      tma_load_3d(stageA(st), &tmX, (int)(kbeg + (long long)tn * K1_BK), m0, zs, bar);
-      if (bzero) {
-        mbar_arrive_expect_tx(bar, 0);
-      } else {
-        mbar_arrive_expect_tx(bar, BBYTES);
-        tma_load_3d(stageB(st), &tmB, (int)(kbeg + (long long)tn * K1_BK), 0, zs, bar);
+  } else {
+    for (int t = 0; t < ntk; ++t) {
+      const int st = t % ST;
+      if (!mbar_wait(smem_u32(&full[st]), (uint32_t)((t / ST) & 1)) || timeout_flag) {
+        timeout_flag = 1;
+        break;
       }
+      if (t == 0) TTRACE_CTA(1);
+      float ss = 0.f;
+#pragma unroll
+      for (int bx = 0; bx < 2; ++bx) {
+        const uint32_t tA = stageA(st) + bx * ABOX, tB = stageB(st) + bx * BBOX;
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk) {
+          uint32_t af[4];
+          {
+            const int row = wr * 16 + (lane & 15);
+            ldsm_x4(tA + swz(row, kk * 2 + (lane >> 4)), af[0], af[1], af[2], af[3]);
+          }
+          if (wc == 0) ss += frag_sumsq<TX>(af);
+#pragma unroll
+          for (int p = 0; p < NT / 2; ++p) {
+            uint32_t b0, b1, b2, b3;
+            const int n = wc * (NP / 2) + p * 16 + (lane & 7) + ((lane >> 4) << 3);
+            ldsm_x4(tB + swz(n, kk * 2 + ((lane >> 3) & 1)), b0, b1, b2, b3);
+            mma16816<TX>(acc[2 * p], af, b0, b1);
+            mma16816<TX>(acc[2 * p + 1], af, b2, b3);
+          }
+          if constexpr (NT % 2 == 1) {
+            uint32_t b0, b1;
+            const int n = wc * (NP / 2) + (NT - 1) * 8 + (lane & 7);
+            ldsm_x2(tB + swz(n, kk * 2 + ((lane >> 3) & 1)), b0, b1);
+            mma16816<TX>(acc[NT - 1], af, b0, b1);
+          }
+        }
+      }
+      two_sum_acc(ssh, ssl, ss);
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(&empty[st]));   // this warp is done with stage st
     }
   }
-  if (t_done < ntk) {
-    // a wait gave up: wait (bounded) for the copies still in flight before the buffers are
-    // reused, then finish the cluster protocol with the step marked failed (ETIMEOUT)
-    for (int t = t_done; t < ntk && t < t_done + K1_STAGES - 1; ++t)
-      mbar_wait(smem_u32(&bars[t % K1_STAGES]), (uint32_t)((t / K1_STAGES) & 1));
-    __syncthreads();
-  }
+  __syncthreads();          // every stage consumed (or the copies in flight drained)
   if (tr0) TTRACE(1);
   TTRACE_CTA(2);
   // ---- partial tile -> shared memory P[BM][NP] (fp32), reusing the pipeline buffers
   float* P = reinterpret_cast<float*>(smem);
-  {
+  if (!producer) {
     const int g = lane >> 2, t4 = lane & 3;
 #pragma unroll
     for (int j = 0; j < NT; ++j) {
@@ -848,9 +884,10 @@ template <int NP>
 __device__ __forceinline__ void env_w2_nx(const float* __restrict__ W2part, int r, float* sD, float* sN,
                                           float* W2st, bool write_state) {
   const int tid = threadIdx.x;
+  const bool worker = tid < K2_THREADS;       // extra (producer) warps only synchronise
   constexpr int PER = (NP * NP + K2_THREADS - 1) / K2_THREADS;
   constexpr int G = PER < 4 ? PER : 4;       // elements whose partials are loaded together
-  for (int u0 = 0; u0 < PER; u0 += G) {
+  for (int u0 = 0; worker && u0 < PER; u0 += G) {
   float v[G][KB_CLUSTER];
 #pragma unroll
   for (int u = 0; u < G; ++u) {
@@ -876,7 +913,7 @@ __device__ __forceinline__ void env_w2_nx(const float* __restrict__ W2part, int 
   }
   __syncthreads();
   constexpr int HB = NP / 2;
-  for (int blk = tid; blk < HB * HB; blk += K2_THREADS) {
+  for (int blk = tid; worker && blk < HB * HB; blk += K2_THREADS) {
     const int i0 = 2 * (blk / HB), j0 = 2 * (blk % HB);
     float c00 = 0.f, c01 = 0.f, c10 = 0.f, c11 = 0.f;
 #pragma unroll
@@ -1426,16 +1463,20 @@ __global__ void __launch_bounds__(K2_THREADS, 1)
 }
 
 // ================================================================ K2 (streamed row stages)
-// F^T = X_(1)^T Q1 for a 64-column tile of X, the I_1 rows streamed through a pipeline of
-// 64-row stages: X by TMA (the solve kernel's 64 x 64 boxes; the first stages are requested
-// before the dependency wait), Q1 rows by cp.async into an XOR-swizzled layout.  The 8 warps
-// split the 64 x NP output tile (warp w: columns 16 (w % 4).., n8-tiles of half w / 4) and each
-// accumulates over all rows in row order, so no cross-warp reduction is needed.  Small shared
-// memory (two or more CTAs per SM) and long row loops: the kernel for batches of streams,
-// whose grids hold many column tiles.
+// F^T = X_(1)^T Q1 for a 128-column tile of X, the I_1 rows streamed through a pipeline of
+// 64-row stages (two 64 x 64 TMA boxes of X: 256 contiguous bytes of every row, the solve
+// kernel's map; and the stage's Q1 rows by cp.async into an XOR-swizzled layout).  Warp 8
+// issues the copies (the first X stages before the dependency wait) and both kinds complete
+// on the stage's `full` barrier; warps 0-7 each own 16 output columns for all NP, accumulate
+// over the rows in row order (no cross-warp reduction) and release stages through `empty`.
+// Small shared memory (two CTAs per SM) and long row loops: the kernel for batches.
 constexpr int K2P_BM = 64;            // rows of X per stage
+constexpr int K2P_BN = 128;           // slice columns j per CTA
+constexpr int K2P_CWARPS = 8;
+constexpr int K2P_THREADS = (K2P_CWARPS + 1) * 32;
+constexpr int K2P_MAXST = 4;
 template <int NP>
-__host__ __device__ constexpr int k2p_stages() { return NP <= 32 ? 6 : 4; }
+__host__ __device__ constexpr int k2p_stages() { return NP <= 32 ? 4 : 3; }
 // bytes per Q1 row in a stage: NP 16-bit values, rows of 48 padded to 64 (128 B)
 template <int NP>
 __host__ __device__ constexpr int k2p_qrow() { return NP == 48 ? 128 : NP * 2; }
@@ -1447,22 +1488,25 @@ __device__ __forceinline__ uint32_t k2p_qaddr(int row, int c) {
 }
 template <int NP>
 __host__ __device__ constexpr size_t k2p_smem_bytes() {
-  // X stages (64 x 128 B, 128B-swizzled) | Q1 stages (64 rows) | Nx, D2 (NP x NP each);
-  // my columns of F (64 x (r+1) floats) reuse the X stages after the loop
-  return 1024 + (size_t)k2p_stages<NP>() * (K2P_BM * 128 + K2P_BM * k2p_qrow<NP>()) + (size_t)2 * NP * NP * 4;
+  // X stages (64 x 256 B: two 128B-swizzled boxes) | Q1 stages (64 rows) | Nx, D2 (NP x NP
+  // each); my columns of F (128 x (r+1) floats) reuse the X stages after the loop
+  return 1024 + (size_t)k2p_stages<NP>() * (K2P_BM * 256 + K2P_BM * k2p_qrow<NP>()) + (size_t)2 * NP * NP * 4;
+}
+__device__ __forceinline__ void cp_async_mbar_arrive_noinc(uint32_t bar) {
+  asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];\n" ::"r"(bar) : "memory");
 }
 
 template <typename TX, int NP>
-__global__ void __launch_bounds__(K2_THREADS, 2)
+__global__ void __launch_bounds__(K2P_THREADS, 2)
     k_fast_env_stream(const __grid_constant__ CUtensorMap tmX, EnvArgs a0) {
   const int zs = blockIdx.z;
   const EnvArgs a = env_args_for_stream<TX, NP>(a0, zs, gridDim.x * gridDim.y);
   constexpr int ST = k2p_stages<NP>();
-  constexpr int NT8 = NP / 8;         // n8-tiles of the output tile
-  constexpr int NTW = NT8 / 2;        // n8-tiles per warp
+  static_assert(ST <= K2P_MAXST, "stages");
+  constexpr int NT8 = NP / 8;         // n8-tiles of the output (every warp covers all NP)
   constexpr int CPR = NP / 8;         // 16-byte chunks per Q1 row
-  constexpr uint32_t XB = K2P_BM * 128, QB = K2P_BM * k2p_qrow<NP>();
-  static_assert(K2S_BN == 64 && K2_THREADS == 256, "warp tiling assumes 64 columns and 8 warps");
+  constexpr uint32_t XBOX = K2P_BM * 128, XB = 2 * XBOX, QB = K2P_BM * k2p_qrow<NP>();
+  static_assert(NT8 % 2 == 0, "n8-tiles come in pairs");
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
   const int M = a.M, r = a.r, rr = r * r;
@@ -1471,33 +1515,52 @@ __global__ void __launch_bounds__(K2_THREADS, 2)
   float* sN = reinterpret_cast<float*>(smem + ST * (XB + QB)); // Nx, NP x NP, zero past r
   float* sW = sN + NP * NP;                                    // D2 = W2 - I (NP x NP)
   const int LDF = r + 1;
-  float* sF = reinterpret_cast<float*>(smem);                  // [64][r+1] after the loop
-  __shared__ __align__(8) uint64_t bars[ST];
+  float* sF = reinterpret_cast<float*>(smem);                  // [128][r+1] after the loop
+  __shared__ __align__(8) uint64_t full[K2P_MAXST];
+  __shared__ __align__(8) uint64_t empty[K2P_MAXST];
   __shared__ float redf[64];
   __shared__ int last_flag;
   __shared__ int timeout_flag;
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const bool producer = (warp == K2P_CWARPS);
   const int ct = blockIdx.x;
-  const long long j0 = (long long)ct * K2S_BN;
-  const int xcols = (a.J - j0 < K2S_BN) ? (int)(a.J - j0) : K2S_BN;
+  const long long j0 = (long long)ct * K2P_BN;
+  const int xcols = (a.J - j0 < K2P_BN) ? (int)(a.J - j0) : K2P_BN;
   const int nt = (M + K2P_BM - 1) / K2P_BM;
   const bool tr0 = (blockIdx.x == 0);
   const bool W2_WRITER = (blockIdx.x == 0);   // one CTA writes the state's W2
+  auto load_x = [&](int t, int st) {          // producer lane 0
+    const uint32_t bar = smem_u32(&full[st]);
+    mbar_arrive_expect_tx(bar, XB);
+    tma_load_3d(xs + st * XB, &tmX, (int)j0, t * K2P_BM, zs, bar);
+    tma_load_3d(xs + st * XB + XBOX, &tmX, (int)j0 + 64, t * K2P_BM, zs, bar);
+  };
+  const TX* Qh = (const TX*)a.Qh;
+  auto load_q = [&](int t, int st) {          // the 32 producer lanes
+    const uint32_t dst = qs + (uint32_t)st * QB;
+    for (int c = lane; c < K2P_BM * CPR; c += 32) {
+      const int lr = c / CPR, ch = c % CPR;
+      const int row = t * K2P_BM + lr;
+      const bool ok = row < M;
+      cp_async16(dst + k2p_qaddr<NP>(lr, ch), Qh + (ok ? (long long)row * NP + ch * 8 : 0), ok ? 16u : 0u);
+    }
+    cp_async_mbar_arrive_noinc(smem_u32(&full[st]));
+  };
 
-  // 1. the first X stages (independent of the previous kernels)
+  // 1. barriers; the first X stages (independent of the previous kernels)
   if (tid == 0) {
     asm volatile("prefetch.tensormap [%0];\n" ::"l"(reinterpret_cast<uint64_t>(&tmX)) : "memory");
-    for (int st = 0; st < ST; ++st) mbar_init(smem_u32(&bars[st]), 1);
+    for (int st = 0; st < ST; ++st) {
+      mbar_init(smem_u32(&full[st]), 1 + 32);      // X expect_tx arrival + 32 lanes' Q1 copies
+      mbar_init(smem_u32(&empty[st]), K2P_CWARPS);
+    }
     mbar_fence_init();
     timeout_flag = 0;
-    for (int st = 0; st < ST && st < nt; ++st) {
-      const uint32_t bar = smem_u32(&bars[st]);
-      mbar_arrive_expect_tx(bar, XB);
-      tma_load_3d(xs + st * XB, &tmX, (int)j0, st * K2P_BM, zs, bar);
-    }
   }
   __syncthreads();
+  if (producer && lane == 0)
+    for (int t = 0; t < ST && t < nt; ++t) load_x(t, t);
   if (tr0) TTRACE(20);
   // 2. wait for the factor kernel (Q1, W2 partials, ctl)
   pdl_wait();
@@ -1513,8 +1576,8 @@ __global__ void __launch_bounds__(K2_THREADS, 2)
   }
   if (a.ctl->skip) {
     // non-finite slice: the new state is the old one
-    const long long nthr = (long long)gridDim.x * K2_THREADS;
-    const long long me = (long long)blockIdx.x * K2_THREADS + tid;
+    const long long nthr = (long long)gridDim.x * blockDim.x;
+    const long long me = (long long)blockIdx.x * blockDim.x + tid;
     for (long long e = me; e < (long long)M * r; e += nthr) a.Qst[e] = a.Qold[e];
     for (long long e = me; e < (long long)r * a.J; e += nthr) {
       a.Cst[e] = a.Cold[e];
@@ -1522,87 +1585,84 @@ __global__ void __launch_bounds__(K2_THREADS, 2)
     }
     for (long long e = me; e < rr; e += nthr) a.W2st[e] = a.W2old[e];
     if (me == 0) *a.ch_shift = *a.ch_shift_old;
-    bool ok = true;
-    for (int st = 0; st < ST && st < nt; ++st) ok = mbar_wait(smem_u32(&bars[st]), 0) && ok;
-    if (!ok && tid == 0) a.ctl->latched = 5;
+    if (producer) {
+      // the X copies in flight land before the CTA exits: the lanes stand in for the Q1
+      // arrivals that never come, then lane 0 waits (bounded) for each stage's phase
+      for (int st = 0; st < ST && st < nt; ++st) mbar_arrive(smem_u32(&full[st]));
+      bool ok = true;
+      if (lane == 0)
+        for (int st = 0; st < ST && st < nt; ++st) ok = mbar_wait(smem_u32(&full[st]), 0) && ok;
+      if (!ok) a.ctl->latched = 5;
+    }
     return;
   }
-  // Q1 rows [64 t, 64 t + 64) into Q stage t % ST (rows past I_1 zero)
-  const TX* Qh = (const TX*)a.Qh;
-  auto load_q = [&](int t) {
-    const uint32_t dst = qs + (uint32_t)(t % ST) * QB;
-    for (int c = tid; c < K2P_BM * CPR; c += K2_THREADS) {
-      const int lr = c / CPR, ch = c % CPR;
-      const int row = t * K2P_BM + lr;
-      const bool ok = row < M;
-      cp_async16(dst + k2p_qaddr<NP>(lr, ch), Qh + (ok ? (long long)row * NP + ch * 8 : 0), ok ? 16u : 0u);
+  if (producer) {
+    // Q1 of the first stages, then the rest of the pipeline
+    for (int t = 0; t < ST && t < nt; ++t) load_q(t, t);
+    int issued = nt < ST ? nt : ST;
+    for (int t = ST; t < nt; ++t) {
+      const int st = t % ST;
+      bool ok = true;
+      if (lane == 0) ok = mbar_wait(smem_u32(&empty[st]), (uint32_t)(((t / ST) - 1) & 1)) && !timeout_flag;
+      ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+      if (!ok) {
+        if (lane == 0) timeout_flag = 1;
+        break;
+      }
+      load_q(t, st);
+      if (lane == 0) load_x(t, st);
+      issued = t + 1;
     }
-  };
-  for (int t = 0; t < ST - 1; ++t) {
-    if (t < nt) load_q(t);
-    cp_async_commit();
+    cp_async_wait<0>();
+    if (lane == 0 && timeout_flag) {
+      // a wait gave up: wait (bounded) for the copies still in flight before the buffers are
+      // reused; the step is marked failed (ETIMEOUT)
+      for (int t = issued - ST > 0 ? issued - ST : 0; t < issued; ++t)
+        mbar_wait(smem_u32(&full[t % ST]), (uint32_t)((t / ST) & 1));
+    }
   }
   env_w2_nx<NP>(a.W2part, r, sW, sN, a.W2st, W2_WRITER);
   if (tr0) TTRACE(22);
-  // 3. F^T (64 x NP) = X^T Q1 over the row stages
-  const int wm = warp & 3, wn = (warp >> 2) * NTW;
-  float acc[NTW][4];
+  // 3. F^T (128 x NP) = X^T Q1 over the row stages: warp w owns columns 16 w .. 16 w + 15
+  float acc[NT8][4];
 #pragma unroll
-  for (int n = 0; n < NTW; ++n) acc[n][0] = acc[n][1] = acc[n][2] = acc[n][3] = 0.f;
-  int t_done = nt;
-  for (int t = 0; t < nt; ++t) {
-    const int st = t % ST;
-    if (t + ST - 1 < nt) load_q(t + ST - 1);     // its buffer was released at the end of t - 1
-    cp_async_commit();
-    cp_async_wait<ST - 1>();                     // this thread's copies of stage t landed
-    if (!mbar_wait(smem_u32(&bars[st]), (uint32_t)((t / ST) & 1))) timeout_flag = 1;
-    __syncthreads();
-    const uint32_t xst = xs + st * XB, qst = qs + st * QB;
+  for (int n = 0; n < NT8; ++n) acc[n][0] = acc[n][1] = acc[n][2] = acc[n][3] = 0.f;
+  if (!producer) {
+    const uint32_t xoff = (uint32_t)(warp >> 2) * XBOX;   // box of my columns
+    const int wm = warp & 3;                              // m16-tile within the box
+    for (int t = 0; t < nt; ++t) {
+      const int st = t % ST;
+      if (!mbar_wait(smem_u32(&full[st]), (uint32_t)((t / ST) & 1)) || timeout_flag) {
+        timeout_flag = 1;
+        break;
+      }
+      const uint32_t xst = xs + st * XB + xoff, qst = qs + st * QB;
 #pragma unroll
-    for (int k0 = 0; k0 < K2P_BM; k0 += 16) {
-      uint32_t af[4];
-      {
-        const int row = k0 + (lane & 7) + ((lane >> 4) << 3);
-        ldsm_x4_t(xst + swz(row, 2 * wm + ((lane >> 3) & 1)), af[0], af[1], af[2], af[3]);
-      }
-      const int qrow = k0 + (lane & 7) + (((lane >> 3) & 1) << 3);
+      for (int k0 = 0; k0 < K2P_BM; k0 += 16) {
+        uint32_t af[4];
+        {
+          const int row = k0 + (lane & 7) + ((lane >> 4) << 3);
+          ldsm_x4_t(xst + swz(row, 2 * wm + ((lane >> 3) & 1)), af[0], af[1], af[2], af[3]);
+        }
+        const int qrow = k0 + (lane & 7) + (((lane >> 3) & 1) << 3);
 #pragma unroll
-      for (int p = 0; p < NTW / 2; ++p) {
-        uint32_t b0, b1, b2, b3;
-        ldsm_x4_t(qst + k2p_qaddr<NP>(qrow, wn + 2 * p + (lane >> 4)), b0, b1, b2, b3);
-        mma16816<TX>(acc[2 * p], af, b0, b1);
-        mma16816<TX>(acc[2 * p + 1], af, b2, b3);
+        for (int p = 0; p < NT8 / 2; ++p) {
+          uint32_t b0, b1, b2, b3;
+          ldsm_x4_t(qst + k2p_qaddr<NP>(qrow, 2 * p + (lane >> 4)), b0, b1, b2, b3);
+          mma16816<TX>(acc[2 * p], af, b0, b1);
+          mma16816<TX>(acc[2 * p + 1], af, b2, b3);
+        }
       }
-      if constexpr (NTW % 2 == 1) {
-        uint32_t b0, b1;
-        ldsm_x2_t(qst + k2p_qaddr<NP>(qrow, wn + NTW - 1), b0, b1);
-        mma16816<TX>(acc[NTW - 1], af, b0, b1);
-      }
-    }
-    __syncthreads();                             // every warp is done with stage st
-    if (timeout_flag) {                          // uniform (read after the barrier)
-      t_done = t + 1;
-      break;
-    }
-    if (tid == 0 && t + ST < nt) {
-      const uint32_t bar = smem_u32(&bars[st]);
-      mbar_arrive_expect_tx(bar, XB);
-      tma_load_3d(xst, &tmX, (int)j0, (t + ST) * K2P_BM, zs, bar);
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(&empty[st]));   // this warp is done with stage st
     }
   }
-  cp_async_wait<0>();
-  if (t_done < nt) {
-    // a wait gave up: wait (bounded) for the X stages still in flight before the buffers are
-    // reused, then finish with the step marked failed (ETIMEOUT)
-    for (int t = t_done; t < nt && t < t_done + ST - 1; ++t)
-      mbar_wait(smem_u32(&bars[t % ST]), (uint32_t)((t / ST) & 1));
-    __syncthreads();
-  }
-  {
+  __syncthreads();          // every stage consumed (or the copies in flight drained)
+  if (!producer) {
     const int g = lane >> 2, t4 = lane & 3;
 #pragma unroll
-    for (int n = 0; n < NTW; ++n) {
-      const int c = (wn + n) * 8 + 2 * t4, jl = wm * 16 + g;
+    for (int n = 0; n < NT8; ++n) {
+      const int c = n * 8 + 2 * t4, jl = warp * 16 + g;
       if (c < r) {
         sF[jl * LDF + c] = acc[n][0];
         sF[(jl + 8) * LDF + c] = acc[n][2];
@@ -1625,7 +1685,7 @@ __global__ void __launch_bounds__(K2_THREADS, 2)
   if (ct == 0 && tid == 0) *a.ch_shift = shift;
   const float scale = ldexpf(1.0f, -shift);
   float ph = 0.f, pl = 0.f;     // float-float partial of ||x^||^2
-  env_columns_out<TX, NP>(sF, LDF, sN, xcols, r, a.J, j0, a.Cst, (TX*)a.Chst, scale, ph, pl);
+  if (!producer) env_columns_out<TX, NP>(sF, LDF, sN, xcols, r, a.J, j0, a.Cst, (TX*)a.Chst, scale, ph, pl);
   const float2 cc_cta = ff_block_sum(ph, pl, redf);
   if (tr0) TTRACE(24);
   // one partial per CTA; the last CTA of the stream's grid sums them in a fixed order
@@ -1640,11 +1700,12 @@ __global__ void __launch_bounds__(K2_THREADS, 2)
   if (!last_flag) return;
   __threadfence();
   float sh = 0.f, sl = 0.f;
-  for (int b0 = tid; b0 < ncta; b0 += 4 * K2_THREADS) {
+  const int nthr = (int)blockDim.x;
+  for (int b0 = tid; b0 < ncta; b0 += 4 * nthr) {
     float2 v[4];
 #pragma unroll
     for (int u = 0; u < 4; ++u)
-      v[u] = (b0 + u * K2_THREADS < ncta) ? __ldcg(a.cc_part + b0 + u * K2_THREADS) : make_float2(0.f, 0.f);
+      v[u] = (b0 + u * nthr < ncta) ? __ldcg(a.cc_part + b0 + u * nthr) : make_float2(0.f, 0.f);
 #pragma unroll
     for (int u = 0; u < 4; ++u) ff_add(sh, sl, v[u].x, v[u].y);
   }
