@@ -1596,9 +1596,13 @@ __global__ void __launch_bounds__(K2P_THREADS, 2)
     }
     return;
   }
-  if (producer) {
-    // Q1 of the first stages, then the rest of the pipeline
+  // Q1 of the first stages; W2 and Nx (a block-wide step) while the copies fly; then the
+  // producer refills stages as they are released and the consumers run the row loop
+  if (producer)
     for (int t = 0; t < ST && t < nt; ++t) load_q(t, t);
+  env_w2_nx<NP>(a.W2part, r, sW, sN, a.W2st, W2_WRITER);
+  if (tr0) TTRACE(22);
+  if (producer) {
     int issued = nt < ST ? nt : ST;
     for (int t = ST; t < nt; ++t) {
       const int st = t % ST;
@@ -1621,8 +1625,6 @@ __global__ void __launch_bounds__(K2P_THREADS, 2)
         mbar_wait(smem_u32(&full[t % ST]), (uint32_t)((t / ST) & 1));
     }
   }
-  env_w2_nx<NP>(a.W2part, r, sW, sN, a.W2st, W2_WRITER);
-  if (tr0) TTRACE(22);
   // 3. F^T (128 x NP) = X^T Q1 over the row stages: warp w owns columns 16 w .. 16 w + 15
   float acc[NT8][4];
 #pragma unroll

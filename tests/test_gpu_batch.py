@@ -16,8 +16,10 @@ from paper_2606_31061_b300 import synth
 
 pytestmark = pytest.mark.gpu
 
+# small shapes (fewer row and column stages than the pipelines hold) and 384 x 384 (more row
+# stages than the environment kernel's pipeline: its refill path)
 SHAPES = [("video", {"dims": (96, 128, 3)}), ("square", {"s": 128, "r": 16}), ("square", {"s": 192, "r": 40}),
-          ("square", {"s": 160, "r": 64})]
+          ("square", {"s": 160, "r": 64}), ("square", {"s": 384, "r": 16})]
 
 
 def _torch():
@@ -89,6 +91,20 @@ def test_batch_matches_alone(name, kw):
         re_a = np.sqrt(sa[-1][3] / sa[-1][2])
         re_b = np.sqrt(sb[-1][3] / sb[-1][2])
         assert abs(re_a - re_b) <= 1e-3, (name, b, re_a, re_b)
+
+
+def test_batch_full_size_video():
+    """Two 1080 x 1920 x 3 video streams: both pipelines run their refill paths."""
+    torch = _torch()
+    nb, T = 2, 3
+    ss = [_stream("video", {}, b, T) for b in range(nb)]
+    dims, ranks = ss[0][0], ss[0][1]
+    batch = _run_batch(torch, dims, ranks, [(s[2], s[3], s[4]) for s in ss])
+    for b, s in enumerate(ss):
+        xa, sa = _run_alone(torch, dims, ranks, s[2], s[3], s[4])
+        for t in range(T):
+            rel = np.linalg.norm(batch[b][0][t] - xa[t]) / np.linalg.norm(xa[t])
+            assert rel <= 1e-3, (b, t, rel)
 
 
 @pytest.mark.parametrize("name,kw", SHAPES[:2])
