@@ -403,10 +403,13 @@ struct Impl final : ttals_stream {
       return TTALS_OK;
     }
     k1_rows = (int)cdiv(M, fast::K1_BM);
-    // k-splits of the solve: enough CTAs for two per SM over the whole batch, and no more
-    // (a batch fills the GPU with row tiles; fewer splits mean longer, cheaper CTAs)
+    // k-splits of the solve: up to two CTAs per SM over the whole batch, and clusters of 8
+    // only while they fit one CTA per SM (more of them do not all fit the GPCs at once); a
+    // batch that fills the GPU with row tiles takes none (longer CTAs, no cluster reduction)
     k1_split = 8;
-    while (k1_split > 1 && (long long)k1_rows * k1_split * nbatch > 2 * kSMs) k1_split >>= 1;
+    while (k1_split > 1 && ((long long)k1_rows * k1_split * nbatch > 2 * kSMs ||
+                            (k1_split == 8 && (long long)k1_rows * k1_split * nbatch > kSMs)))
+      k1_split >>= 1;
     k1_kchunk = cdiv(cdiv(J, k1_split), fast::K1_BK) * fast::K1_BK;
     k2_cols = (int)cdiv(J, fast::K2_BN);
     // row chunks per cluster: the fewest (largest chunks) that keep two env CTAs per SM
