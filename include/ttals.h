@@ -64,7 +64,12 @@ typedef struct {
     int qr_passes;       /* orthogonalisation passes per local solve: 1 = Cholesky-QR with an
                             FP32 factor only, 2 = followed by one FP64 polar
                             re-orthogonalisation (0 = default = 2)                        */
-    int reserved[4];     /* must be zero                                                  */
+    int env_kernel;      /* fused path, environment kernel (S6): 0 = chosen by shape, 1 = the
+                            clustered one, 2 = one CTA per column tile over all rows (ignored
+                            when its tile does not fit), 3 = streamed row stages           */
+    int k1_split;        /* fused path, k-splits of the local solve (S4): 0 = chosen by
+                            shape and batch size, else 1, 2, 4 or 8                         */
+    int reserved[2];     /* must be zero                                                  */
 } ttals_config;
 
 /*
@@ -78,7 +83,10 @@ typedef struct {
  * ("Initialize orthogonal cores randomly", Algorithm 1): Gaussian entries from a
  * SplitMix64 / Box-Muller generator seeded with cfg->seed.  Allocates every
  * device buffer the update needs; no later call allocates.
- * Errors: EINVAL (shape, dtype, reserved fields), ENOMEM, ECUDA.  On error *out is NULL.
+ * env_kernel and k1_split fix the fused path's schedule (an autotuner's choice); they change
+ * the FP32 summation order, never the arithmetic the update performs.
+ * Errors: EINVAL (shape, dtype, schedule fields out of range, reserved fields), ENOMEM,
+ * ECUDA.  On error *out is NULL.
  */
 ttals_status ttals_create(int n_slice_modes, const int64_t *dims, const int64_t *ranks,
                           const ttals_config *cfg, ttals_stream **out);
@@ -215,6 +223,10 @@ ttals_status ttals_slice_error_noalloc(const void *x_dev, ttals_dtype x_dtype, c
  * ttals_batch_select - wait for the batch's work, then direct the per-stream calls
  *   (ttals_set_cores, ttals_cores, ttals_reconstruct, ttals_stats, ttals_stats_async,
  *   ttals_step, ttals_sync) to stream `index`.  Errors: EINVAL, ECUDA.
+ * ttals_push_batch_masked - like ttals_push_batch, but only the streams whose bit is set in
+ *   active_mask (bit b for stream b) take a step; the others keep their state, step count
+ *   and statistics, and their part of slices_dev is not read.  For serving loops in which
+ *   not every stream has a new slice at every step.  An all-zero mask enqueues nothing.
  * ttals_batch_size - n_streams of a batch, 1 for a single stream, 0 for NULL.
  * ttals_push_slice on a batch returns ESTATE.
  */
@@ -223,6 +235,8 @@ ttals_status ttals_create_batch(int n_streams, int n_slice_modes, const int64_t 
                                 const int64_t *ranks, const ttals_config *cfg, ttals_stream **out);
 ttals_status ttals_push_batch(ttals_stream *s, const void *slices_dev, ttals_dtype dtype,
                               void *cuda_stream);
+ttals_status ttals_push_batch_masked(ttals_stream *s, const void *slices_dev, ttals_dtype dtype,
+                                     uint64_t active_mask, void *cuda_stream);
 ttals_status ttals_batch_select(ttals_stream *s, int index);
 int ttals_batch_size(const ttals_stream *s);
 

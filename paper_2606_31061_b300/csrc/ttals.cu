@@ -163,6 +163,9 @@ struct ttals_stream {
   Ctl* ctl_base = nullptr;            // [nbatch] control blocks
   int nbatch = 1;                     // streams of a batch (ttals_create_batch), else 1
   int sel = 0;                        // stream that the per-stream calls refer to
+  unsigned long long active_mask = ~0ull;   // streams of a batch that take the next push
+  int cfg_env_kernel = 0;             // ttals_config.env_kernel (0: by shape)
+  int cfg_k1_split = 0;               // ttals_config.k1_split (0: by shape and batch)
   size_t bytes = 0;
   std::vector<void*> allocs;
   unsigned long long nlaunch = 0;      // kernels launched by this stream (host counter)
@@ -410,6 +413,7 @@ struct Impl final : ttals_stream {
     while (k1_split > 1 && ((long long)k1_rows * k1_split * nbatch > 2 * kSMs ||
                             (k1_split == 8 && (long long)k1_rows * k1_split * nbatch > kSMs)))
       k1_split >>= 1;
+    if (cfg_k1_split > 0) k1_split = cfg_k1_split;
     k1_kchunk = cdiv(cdiv(J, k1_split), fast::K1_BK) * fast::K1_BK;
     k2_cols = (int)cdiv(J, fast::K2_BN);
     // row chunks per cluster: the fewest (largest chunks) that keep two env CTAs per SM
@@ -451,6 +455,9 @@ struct Impl final : ttals_stream {
         else if (v == "stream") k2_kind = K2_STREAM;
         else if (v == "single" && fits) k2_kind = K2_SINGLE;
       }
+      if (cfg_env_kernel == 1) k2_kind = K2_CLUSTER;          // the stream's config wins
+      else if (cfg_env_kernel == 2 && fits) k2_kind = K2_SINGLE;
+      else if (cfg_env_kernel == 3) k2_kind = K2_STREAM;
       if (k2_kind == K2_SINGLE) {
         k2_nq = 1;
         k2_cols = (int)cdiv(J, fast::K2S_BN);
@@ -581,6 +588,7 @@ struct Impl final : ttals_stream {
       a1.Y = fY;
       a1.xx_part = fXX;
       a1.ctl = ctl_base;
+      a1.active = active_mask;
       cudaLaunchConfig_t c1{};
       c1.gridDim = dim3((unsigned)k1_rows, (unsigned)k1_split, (unsigned)nbatch);
       c1.blockDim = dim3(fast::K1_THREADS, 1, 1);
@@ -605,6 +613,7 @@ struct Impl final : ttals_stream {
       ab.hh_work = fHH;
       ab.Qfb = fQfb;
       ab.ctl = ctl_base;
+      ab.active = active_mask;
       cudaLaunchAttribute atb[2];
       atb[0] = at[0];
       atb[0].val.clusterDim.y = (unsigned)fast::KB_CLUSTER;
@@ -641,6 +650,7 @@ struct Impl final : ttals_stream {
       a2.W2old = fW2b[par];
       a2.ch_shift_old = fShiftb + par;
       a2.is_half = std::is_same<TX, __half>::value ? 1 : 0;
+      a2.active = active_mask;
       at[0].val.clusterDim.y = (unsigned)k2_nq;
       cudaLaunchConfig_t c2{};
       c2.gridDim = dim3((unsigned)k2_cols, (unsigned)k2_nq, (unsigned)nbatch);
@@ -1139,8 +1149,11 @@ static ttals_status create_streams(int nbatch, int n_slice_modes, const int64_t*
   c.device = 0;
   if (cfg) {
     c = *cfg;
-    for (int i = 0; i < 4; ++i)
+    for (int i = 0; i < 2; ++i)
       if (c.reserved[i] != 0) return TTALS_EINVAL;
+    if (c.env_kernel < 0 || c.env_kernel > 3) return TTALS_EINVAL;
+    if (c.k1_split != 0 && c.k1_split != 1 && c.k1_split != 2 && c.k1_split != 4 && c.k1_split != 8)
+      return TTALS_EINVAL;
     if (c.seed == 0) c.seed = 0x5eedull;
   }
   if (c.ingest < TTALS_F64 || c.ingest > TTALS_BF16) return TTALS_EINVAL;
@@ -1193,6 +1206,8 @@ static ttals_status create_streams(int nbatch, int n_slice_modes, const int64_t*
   s->device = c.device;
   s->qr_passes = c.qr_passes ? c.qr_passes : 2;
   s->nbatch = nbatch;
+  s->cfg_env_kernel = c.env_kernel;
+  s->cfg_k1_split = c.k1_split;
   if (cudaEventCreateWithFlags(&s->ev, cudaEventDisableTiming) != cudaSuccess) {
     delete s;
     return TTALS_ECUDA;
@@ -1251,6 +1266,23 @@ ttals_status ttals_push_batch(ttals_stream* s, const void* slices_dev, ttals_dty
   cudaStream_t st = (cudaStream_t)cuda_stream;
   TT_TRY(s->order_after_last(st));
   return s->push(slices_dev, st);
+}
+
+ttals_status ttals_push_batch_masked(ttals_stream* s, const void* slices_dev, ttals_dtype dtype,
+                                     uint64_t active_mask, void* cuda_stream) {
+  if (!s || !slices_dev) return TTALS_EINVAL;
+  if (dtype != s->ingest) return TTALS_EINVAL;
+  if (((uintptr_t)slices_dev & 15u) != 0) return TTALS_EINVAL;
+  const unsigned long long all = s->nbatch >= 64 ? ~0ull : ((1ull << s->nbatch) - 1ull);
+  const unsigned long long m = (unsigned long long)active_mask & all;
+  if (m == 0) return TTALS_OK;
+  TT_TRY(set_device(s->device));
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  TT_TRY(s->order_after_last(st));
+  s->active_mask = m;
+  const ttals_status r = s->push(slices_dev, st);
+  s->active_mask = ~0ull;
+  return r;
 }
 
 ttals_status ttals_batch_select(ttals_stream* s, int index) {

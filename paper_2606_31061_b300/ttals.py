@@ -17,6 +17,7 @@ LIB_PATH = os.path.join(_HERE, "libttals.so")
 
 F64, F32, F16, BF16 = 0, 1, 2, 3
 DTYPES = {"f64": F64, "f32": F32, "f16": F16, "bf16": BF16}
+MAX_BATCH = 64          # TTALS_MAX_BATCH: streams per ttals_create_batch
 STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENONFINITE", 5: "ETIMEOUT", 6: "ESTATE"}
 
 # every symbol include/ttals.h declares (checked by the ABI test)
@@ -25,7 +26,7 @@ EXPORTS = ("ttals_create", "ttals_destroy", "ttals_effective_ranks", "ttals_set_
            "ttals_sync", "ttals_device_bytes", "ttals_status_string", "ttals_last_error",
            "ttals_launch_count", "ttals_stats_async", "ttals_profile", "ttals_profile_read",
            "ttals_slice_error_noalloc", "ttals_create_batch", "ttals_push_batch", "ttals_batch_select",
-           "ttals_batch_size")
+           "ttals_batch_size", "ttals_push_batch_masked")
 
 
 class TTALSError(RuntimeError):
@@ -37,7 +38,8 @@ class TTALSError(RuntimeError):
 
 class Config(ctypes.Structure):
     _fields_ = [("ingest", ctypes.c_int), ("seed", ctypes.c_uint64), ("device", ctypes.c_int),
-                ("qr_passes", ctypes.c_int), ("reserved", ctypes.c_int * 4)]
+                ("qr_passes", ctypes.c_int), ("env_kernel", ctypes.c_int), ("k1_split", ctypes.c_int),
+                ("reserved", ctypes.c_int * 2)]
 
 
 _lib = None
@@ -74,6 +76,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "ttals_create_batch": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, I64P, I64P, P(Config), P(VP)]),
         "ttals_push_batch": (ctypes.c_int, [VP, VP, ctypes.c_int, VP]),
         "ttals_batch_select": (ctypes.c_int, [VP, ctypes.c_int]),
+        "ttals_push_batch_masked": (ctypes.c_int, [VP, VP, ctypes.c_int, ctypes.c_uint64, VP]),
         "ttals_batch_size": (ctypes.c_int, [VP]),
     }
     for name, (res, args) in sig.items():
@@ -109,11 +112,12 @@ class Stream:
     per-stream methods then refer to the stream chosen by select()."""
 
     def __init__(self, dims: Sequence[int], ranks: Sequence[int], ingest: str = "f64",
-                 seed: int = 0x5EED, device: int = 0, qr_passes: int = 0, n_streams: int = 0):
+                 seed: int = 0x5EED, device: int = 0, qr_passes: int = 0, n_streams: int = 0,
+                 env_kernel: int = 0, k1_split: int = 0):
         lib = load()
         self.dims = tuple(int(d) for d in dims)
         self.ingest = ingest
-        cfg = Config(DTYPES[ingest], seed, device, qr_passes, (ctypes.c_int * 4)(0, 0, 0, 0))
+        cfg = Config(DTYPES[ingest], seed, device, qr_passes, env_kernel, k1_split, (ctypes.c_int * 2)(0, 0))
         h = ctypes.c_void_p()
         if n_streams > 0:
             code = lib.ttals_create_batch(int(n_streams), len(self.dims), _i64(self.dims), _i64(ranks),
@@ -216,14 +220,21 @@ class Stream:
         _check(load().ttals_stats_async(self._h, ctypes.c_void_p(out_ptr),
                                         ctypes.c_void_p(_stream_handle(stream))), "ttals_stats_async")
 
-    def push_batch(self, slices, stream=None):
+    def push_batch(self, slices, stream=None, active: Optional[int] = None):
         """ttals_push_batch: one step of every stream; `slices` is a contiguous CUDA tensor of
-        n_streams slices (stream b's slice is slices[b])."""
-        self.push_batch_ptr(slices.data_ptr(), _stream_handle(stream))
+        n_streams slices (stream b's slice is slices[b]).  With `active` (bit b: stream b),
+        only those streams step (ttals_push_batch_masked)."""
+        self.push_batch_ptr(slices.data_ptr(), _stream_handle(stream), active)
 
-    def push_batch_ptr(self, ptr: int, stream_handle: int):
-        _check(load().ttals_push_batch(self._h, ctypes.c_void_p(ptr), DTYPES[self.ingest],
-                                       ctypes.c_void_p(stream_handle)), "ttals_push_batch")
+    def push_batch_ptr(self, ptr: int, stream_handle: int, active: Optional[int] = None):
+        """ttals_push_batch, or ttals_push_batch_masked when `active` (bit b: stream b) is given."""
+        if active is None:
+            _check(load().ttals_push_batch(self._h, ctypes.c_void_p(ptr), DTYPES[self.ingest],
+                                           ctypes.c_void_p(stream_handle)), "ttals_push_batch")
+        else:
+            _check(load().ttals_push_batch_masked(self._h, ctypes.c_void_p(ptr), DTYPES[self.ingest],
+                                                  ctypes.c_uint64(active), ctypes.c_void_p(stream_handle)),
+                   "ttals_push_batch_masked")
 
     def select(self, index: int):
         """ttals_batch_select: later per-stream calls refer to stream `index` of the batch."""
