@@ -372,22 +372,28 @@ struct Impl final : ttals_stream {
     return TTALS_OK;
   }
 
+  // Each kernel's dynamic shared-memory limit is a per-kernel (not per-stream) setting: raise
+  // it once to the device's opt-in maximum, so that streams of any shape (in any creation
+  // order) can launch their own sizes.  The limit only validates launches; occupancy follows
+  // the size a launch asks for.
+  template <typename K>
+  ttals_status raise_smem_limit(K kern) {
+    cudaFuncAttributes fa{};
+    TT_CUDA(cudaFuncGetAttributes(&fa, kern));
+    int optin = 0;
+    TT_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device));
+    TT_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes));
+    return TTALS_OK;
+  }
+
   template <int NP>
   ttals_status set_fast_attrs() {
     if constexpr (kHalfIngest) {
-      TT_CUDA(cudaFuncSetAttribute(fast::k_fast_solve<TX, NP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   (int)k1_smem));
-      if (k2_kind == K2_SINGLE)
-        TT_CUDA(cudaFuncSetAttribute(fast::k_fast_env1<TX, NP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)k2_smem));
-      else if (k2_kind == K2_STREAM)
-        TT_CUDA(cudaFuncSetAttribute(fast::k_fast_env_stream<TX, NP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)k2_smem));
-      else
-        TT_CUDA(cudaFuncSetAttribute(fast::k_fast_env<TX, NP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)k2_smem));
-      TT_CUDA(cudaFuncSetAttribute(fast::k_fast_factor<TX, NP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   (int)fast::k1b_smem_bytes((int)dims[0], rk(1), NP)));
+      TT_TRY(raise_smem_limit(fast::k_fast_solve<TX, NP>));
+      TT_TRY(raise_smem_limit(fast::k_fast_env1<TX, NP>));
+      TT_TRY(raise_smem_limit(fast::k_fast_env_stream<TX, NP>));
+      TT_TRY(raise_smem_limit(fast::k_fast_env<TX, NP>));
+      TT_TRY(raise_smem_limit(fast::k_fast_factor<TX, NP>));
     }
     return TTALS_OK;
   }
