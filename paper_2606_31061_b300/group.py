@@ -2,8 +2,11 @@
 
 Streams of one shape (slice dims, ranks, ingest) share a batch (``ttals_create_batch``): one
 launch of each fused kernel per step serves all of them, whatever their number.  A group
-therefore steps S streams of K distinct shapes with 3K launches; ``capture`` records an
-even number of steps into one CUDA graph, so that a replay costs one graph launch.
+therefore steps S streams of K distinct shapes with 3K launches.  The batches are
+independent, so each runs on a CUDA stream of its own, forked from and joined back into the
+caller's stream: their latency-bound kernel chains overlap on the GPU.  ``capture`` records
+an even number of steps into one CUDA graph (K parallel branches per step), so that a
+replay costs one graph launch.
 
 Each batch's schedule (environment kernel kind, k-splits of the local solve) comes from
 ``tune.best_schedule`` unless ``tune=False``.  The schedule changes only the order of FP32
@@ -69,6 +72,8 @@ class Group:
                     self.where[i] = (len(self.buckets), slot)
                 self.buckets.append(b)
         self._graph = None
+        import torch
+        self._side = [torch.cuda.Stream() for _ in self.buckets]
 
     # -- inputs and stepping
     def slot(self, i: int, p: int = 0):
@@ -79,18 +84,24 @@ class Group:
     def step(self, p: int = 0, active: Optional[set] = None, stream=None):
         """One step of every stream (or of the streams in `active`), slices from ring position p."""
         import torch
-        h = (stream or torch.cuda.current_stream()).cuda_stream
-        for b in self.buckets:
+        main = stream or torch.cuda.current_stream()
+        fork = torch.cuda.Event()
+        fork.record(main)
+        for b, side in zip(self.buckets, self._side):
             blk = b.inputs[p]
-            if active is None:
-                b.stream.push_batch_ptr(blk.data_ptr(), h)
-            else:
+            mask = None
+            if active is not None:
                 mask = 0
                 for slot, i in enumerate(b.members):
                     if i in active:
                         mask |= 1 << slot
-                if mask:
-                    b.stream.push_batch_ptr(blk.data_ptr(), h, mask)
+                if not mask:
+                    continue
+            side.wait_event(fork)
+            b.stream.push_batch_ptr(blk.data_ptr(), side.cuda_stream, mask)
+            join = torch.cuda.Event()
+            join.record(side)
+            main.wait_event(join)
 
     def capture(self, positions: Sequence[int], stream):
         """Record one step per ring position in `positions` (an even count: the state's
