@@ -361,6 +361,119 @@ def c4_arm(steps, depth=4, tune=True):
     return out
 
 
+SERVE_SIZES = ((256, 256), (720, 1280, 3), (1080, 1920, 3))
+
+
+def serve_specs(n=256, seed=1005):
+    """Serving workload: n streams in equal thirds of the three frame sizes, ranks uniform
+    on [8, 48] per bond (seeded)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(n):
+        dims = SERVE_SIZES[i % 3]
+        out.append((dims, tuple(int(v) for v in rng.integers(8, 49, size=len(dims)))))
+    return out
+
+
+def _serve_frames(nframes=6):
+    """Pinned host FP16 frames per size (synthetic: a drifting low-rank field for 256 x 256,
+    the video recipe at 720p and 1080p)."""
+    import torch
+    from paper_2606_31061_b300 import synth
+    pools = {}
+    for dims in SERVE_SIZES:
+        if len(dims) == 2:
+            sp = synth.make_stream("square", s=dims[0], r=16, seed=1005)
+        else:
+            sp = synth.make_stream("video", dims=dims, seed=1005)
+        pools[dims] = [torch.from_numpy(synth.round_to_ingest(x, "f16")[0]).view(torch.float16).pin_memory()
+                       for x in sp.take(nframes)]
+    return pools
+
+
+def serve_arm(seconds=2.0, n=256, lam=30.0, budget=150e9, slots=8):
+    """Continuous-batching serving loop (paper_2606_31061_b300.serve) in real time: n streams,
+    Poisson frame arrivals at `lam` frames/s each for `seconds`, admission by an HBM budget.
+    Latency per frame = detection of its step's completion - arrival.  Also: the drain rate
+    with every frame already queued (capacity), and the per-stream FP64 path's capacity
+    for the same mix of sizes."""
+    import torch
+    from paper_2606_31061_b300 import serve
+    from paper_2606_31061_b300.ttals import Stream
+    specs = serve_specs(n)
+    frames = _serve_frames()
+    rng = np.random.default_rng(1005)
+    events = []
+    for sid in range(n):
+        t = np.cumsum(rng.exponential(1.0 / lam, size=int(lam * seconds * 2) + 8))
+        events += [(float(tt), sid) for tt in t if tt <= seconds]
+    events.sort()
+
+    def run(evts, realtime):
+        srv = serve.Server(int(budget), slots=slots, rank_step=16)
+        admitted = sum(srv.connect(sid, d, r) for sid, (d, r) in enumerate(specs))
+        torch.cuda.synchronize()
+        nxt = {sid: 0 for sid in range(n)}
+        h2d = 0
+        t0 = time.perf_counter()
+        i = 0
+        while i < len(evts) or srv.backlog():
+            now = time.perf_counter() - t0
+            while i < len(evts) and (not realtime or evts[i][0] <= now):
+                ta, sid = evts[i]
+                d = specs[sid][0]
+                f = frames[d][nxt[sid] % len(frames[d])]
+                nxt[sid] += 1
+                srv.submit(sid, f, t0 + (ta if realtime else 0.0))
+                h2d += f.numel() * 2
+                i += 1
+            srv.tick()
+            srv.poll()
+        t1 = time.perf_counter()
+        out = {"frames": len(srv.latencies), "seconds": t1 - t0, "steps": srv.steps, "admitted": admitted,
+               "pools": sum(len(v) for v in srv.pools.values()), "device_gb": srv.used / 1e9,
+               "h2d_gbs": h2d / (t1 - t0) / 1e9, "latency_s": serve.percentiles(srv.latencies)}
+        srv.close()
+        torch.cuda.empty_cache()
+        return out
+
+    rt = run(events, True)
+    cap_events = [(0.0, sid) for sid in range(n) for _ in range(4)]
+    cap = run(cap_events, False)
+    # per-stream FP64 path: one stream per size, device-resident FP64 frames, device-timed
+    fp64 = {}
+    for dims in SERVE_SIZES:
+        st = Stream(dims, (32,) * len(dims), ingest="f64")
+        x = frames[dims][0].cuda().double()
+        for _ in range(2):
+            st.push(x)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(5):
+            st.push(x)
+        e1.record()
+        torch.cuda.synchronize()
+        fp64["x".join(map(str, dims))] = 5 / (e0.elapsed_time(e1) / 1000.0)
+        st.close()
+        del x
+    fp64_mix = 1.0 / sum((1.0 / 3) / v for v in fp64.values())
+    lat = rt["latency_s"]
+    return {
+        "workload": f"{n} streams, sizes in thirds 256x256 / 720x1280x3 / 1080x1920x3, ranks U[8,48] per bond "
+                    f"(rounded up to multiples of 16 for pooling), Poisson arrivals {lam:g} frames/s each for "
+                    f"{seconds:g} s, FP16 ingest, HBM budget {budget / 1e9:g} GB, pools of {slots} slots",
+        "offered_slices_s": len(events) / seconds,
+        "served_slices_s": rt["frames"] / rt["seconds"],
+        "latency_ms": {"p50": lat["p50"] * 1e3 if lat["p50"] is not None else None,
+                       "p99": lat["p99"] * 1e3 if lat["p99"] is not None else None, "n": lat["n"],
+                       "what": "frame arrival -> host detection of its step's completion event"},
+        "realtime": rt, "capacity_slices_s": cap["frames"] / cap["seconds"], "capacity_run": cap,
+        "fp64_plain_per_stream_slices_s": fp64, "fp64_plain_mix_capacity_slices_s": fp64_mix,
+        "vs_fp64_plain_capacity": (cap["frames"] / cap["seconds"]) / fp64_mix,
+    }
+
+
 def e2e_arm(ingest, steps, pool_np, dist_on):
     """Same metric through the C ABI from pinned HOST buffers: per step an H2D copy of the
     slice (copy stream, double-buffered device slot), the push, and an async D2H read of
@@ -466,6 +579,7 @@ def main():
     ap.add_argument("--batch", type=int, default=16, help="streams per batched push (0: skip)")
     ap.add_argument("--batch-steps", type=int, default=400)
     ap.add_argument("--c4-steps", type=int, default=200, help="mixed-shape group steps (0: skip)")
+    ap.add_argument("--serve-seconds", type=float, default=2.0, help="serving-loop traffic (0: skip)")
     args = ap.parse_args()
     rank = env_int("RANK", 0)
     world = env_int("WORLD_SIZE", 1)
@@ -548,6 +662,7 @@ def main():
             "inputs": f"stream b at step t reads pool frame o_t + b; one push reads {S * slice_bytes / 1e6:.0f} MB",
         }
     c4 = c4_arm(args.c4_steps) if args.c4_steps > 0 else None
+    served = serve_arm(args.serve_seconds) if args.serve_seconds > 0 and world == 1 else None
     f32 = None
     if not args.no_f32 and args.ingest != "f32":
         del pool
@@ -595,6 +710,7 @@ def main():
             "clocks": r["clocks"],
             "batched": batched,
             "c4_mixed_shapes": c4,
+            "serving": served,
             "f32_ingest": f32,
             "cpu_baseline": cpu,
         }
