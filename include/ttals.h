@@ -240,6 +240,17 @@ ttals_status ttals_push_batch_masked(ttals_stream *s, const void *slices_dev, tt
 ttals_status ttals_batch_select(ttals_stream *s, int index);
 int ttals_batch_size(const ttals_stream *s);
 
+/*
+ * ttals_widen_u8 - enqueue on cuda_stream dst[i] = src[i] for n 8-bit unsigned values,
+ *   widened to dst_dtype (F16, BF16 or F32; exact, since 0..255 are representable).
+ *   The paper's video slices are 8-bit pixels (Sec. 5.1): a serving loop that receives
+ *   them from the host can move bytes over the host link and widen on the device, half
+ *   the traffic of FP16.  src and dst: device memory, 16-byte aligned, owned by the
+ *   caller.  Errors (nothing enqueued): EINVAL, ECUDA.
+ */
+ttals_status ttals_widen_u8(const void *src_dev, void *dst_dev, ttals_dtype dst_dtype, int64_t n,
+                            void *cuda_stream);
+
 /* Static text for a status code. */
 const char *ttals_status_string(ttals_status st);
 

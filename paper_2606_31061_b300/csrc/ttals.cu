@@ -1438,6 +1438,30 @@ ttals_status ttals_profile_read(ttals_stream* s, double ms_out[4], int64_t* n_ou
   return TTALS_OK;
 }
 
+ttals_status ttals_widen_u8(const void* src_dev, void* dst_dev, ttals_dtype dst_dtype, int64_t n,
+                            void* cuda_stream) {
+  if (!src_dev || !dst_dev || n < 0) return TTALS_EINVAL;
+  if (dst_dtype != TTALS_F16 && dst_dtype != TTALS_BF16 && dst_dtype != TTALS_F32) return TTALS_EINVAL;
+  if (((uintptr_t)src_dev & 15u) != 0 || ((uintptr_t)dst_dev & 15u) != 0) return TTALS_EINVAL;
+  if (n == 0) return TTALS_OK;
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  const long long n16 = (n + 15) / 16;
+  int dev = 0;
+  TT_CUDA(cudaGetDevice(&dev));
+  int nsm = 0;
+  TT_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  const int nb = (int)std::min<long long>((n16 + 255) / 256, 8LL * nsm);
+  switch (dst_dtype) {
+    case TTALS_F16: k_widen_u8<__half><<<nb, 256, 0, st>>>((const uint8_t*)src_dev, (__half*)dst_dev, n); break;
+    case TTALS_BF16:
+      k_widen_u8<__nv_bfloat16><<<nb, 256, 0, st>>>((const uint8_t*)src_dev, (__nv_bfloat16*)dst_dev, n);
+      break;
+    default: k_widen_u8<float><<<nb, 256, 0, st>>>((const uint8_t*)src_dev, (float*)dst_dev, n); break;
+  }
+  TT_CUDA(cudaGetLastError());
+  return TTALS_OK;
+}
+
 ttals_status ttals_slice_error_noalloc(const void* x_dev, ttals_dtype x_dtype, const void* y_dev,
                                        ttals_dtype y_dtype, int64_t n, double* out2_dev, void* cuda_stream) {
   if (!x_dev || !y_dev || !out2_dev || n < 1) {

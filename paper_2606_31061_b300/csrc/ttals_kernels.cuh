@@ -701,4 +701,30 @@ __global__ void k_norm2_to_cc(const TC* __restrict__ c, long long n, Ctl* __rest
   if (threadIdx.x == 0) ctl->cc = tot;
 }
 
+// 8-bit pixels -> the ingest type (exact: every integer 0..255 is representable in FP16,
+// BF16 and FP32).  16 bytes loaded per thread and step, grid-stride; the tail of n % 16
+// elements is handled element by element by the thread that owns the last chunk.
+template <typename TD>
+__global__ void __launch_bounds__(256) k_widen_u8(const uint8_t* __restrict__ src, TD* __restrict__ dst, long long n) {
+  const long long n16 = n / 16;
+  for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < n16; c += (long long)gridDim.x * blockDim.x) {
+    const uint4 v = __ldcs(reinterpret_cast<const uint4*>(src) + c);
+    const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+    TD o[16];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) o[q] = from_acc<TD>((float)((w[q >> 2] >> (8 * (q & 3))) & 0xffu));
+    if constexpr (sizeof(TD) == 2) {
+      uint4* d = reinterpret_cast<uint4*>(dst + c * 16);
+      d[0] = *reinterpret_cast<const uint4*>(&o[0]);
+      d[1] = *reinterpret_cast<const uint4*>(&o[8]);
+    } else {
+      uint4* d = reinterpret_cast<uint4*>(dst + c * 16);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) d[q] = *reinterpret_cast<const uint4*>(&o[4 * q]);
+    }
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0)
+    for (long long e = n16 * 16; e < n; ++e) dst[e] = from_acc<TD>((float)src[e]);
+}
+
 }  // namespace ttals

@@ -17,6 +17,9 @@ with continuous batching:
   frame step) on the pool's compute stream.  Pools have their own CUDA streams, so the
   work of different pools overlaps on the GPU; frames that arrive while a step is in
   flight wait for the pool's next tick.
+* **Wire format.** With ``wire="u8"`` frames are 8-bit pixels (the paper's video data):
+  bytes cross the host link and ``ttals_widen_u8`` widens them to the ingest type on the
+  device (exact), half the host-link traffic of FP16 frames.
 * **Latency.** Per frame: from its arrival time to the host's detection of the completion
   event of the step that consumed it (``poll()``), in seconds.
 
@@ -54,13 +57,16 @@ def feasible_ranks(dims: Sequence[int], ranks: Sequence[int]) -> Tuple[int, ...]
 class _Pool:
     """Device side of a pool: batch, input blocks, CUDA streams and events."""
 
-    def __init__(self, dims, ranks, slots, ingest):
+    def __init__(self, dims, ranks, slots, ingest, wire="f16"):
         import torch
         from .ttals import Stream
         self.dims, self.ranks, self.slots = tuple(dims), tuple(ranks), int(slots)
         self.batch = Stream(dims, ranks, ingest=ingest, n_streams=self.slots)
         dt = torch.float16 if ingest == "f16" else torch.bfloat16
         self.inputs = torch.zeros((2, self.slots) + self.dims, dtype=dt, device="cuda")
+        self.wire = wire
+        self.stage = (torch.zeros((2, self.slots) + self.dims, dtype=torch.uint8, device="cuda")
+                      if wire == "u8" else None)
         self.copy = torch.cuda.Stream()
         self.comp = torch.cuda.Stream()
         self.copied = [torch.cuda.Event() for _ in range(2)]
@@ -69,6 +75,8 @@ class _Pool:
             e.record(self.comp)
         self.flip = 0
         self.bytes = self.batch.device_bytes + self.inputs.numel() * self.inputs.element_size()
+        if self.stage is not None:
+            self.bytes += self.stage.numel()
 
     def reset_slot(self, slot, sid, init_cores=None):
         """A new stream in this slot: its initial cores (seeded by the stream id unless
@@ -90,7 +98,12 @@ class _Pool:
         with torch.cuda.stream(self.copy):
             self.copy.wait_event(self.consumed[p])
             for slot, f in frames.items():
-                blk[slot].copy_(f, non_blocking=True)
+                if self.stage is None:
+                    blk[slot].copy_(f, non_blocking=True)
+                else:
+                    from .ttals import widen_u8
+                    self.stage[p, slot].copy_(f, non_blocking=True)
+                    widen_u8(self.stage[p, slot], blk[slot], stream=self.copy)
             self.copied[p].record(self.copy)
         self.comp.wait_event(self.copied[p])
         mask = 0
@@ -108,13 +121,14 @@ class _Pool:
 
 class Server:
     def __init__(self, budget_bytes: int, ingest: str = "f16", slots: int = 16, rank_step: int = 16,
-                 pool_factory: Optional[Callable] = None, init_cores: Optional[Callable] = None):
+                 pool_factory: Optional[Callable] = None, init_cores: Optional[Callable] = None,
+                 wire: str = "f16"):
         self.budget = int(budget_bytes)
         self.used = 0
         self.ingest = ingest
         self.slots = int(slots)
         self.rank_step = int(rank_step)
-        self.pool_factory = pool_factory or (lambda d, r, n: _Pool(d, r, n, ingest))
+        self.pool_factory = pool_factory or (lambda d, r, n: _Pool(d, r, n, ingest, wire))
         self.init_cores = init_cores           # (stream_id, dims, ranks) -> (cores, g), or seeded
         self.pools: Dict[tuple, List[object]] = collections.defaultdict(list)
         self.where: Dict[object, Tuple[object, int]] = {}     # stream id -> (pool, slot)

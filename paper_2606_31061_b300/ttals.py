@@ -26,7 +26,7 @@ EXPORTS = ("ttals_create", "ttals_destroy", "ttals_effective_ranks", "ttals_set_
            "ttals_sync", "ttals_device_bytes", "ttals_status_string", "ttals_last_error",
            "ttals_launch_count", "ttals_stats_async", "ttals_profile", "ttals_profile_read",
            "ttals_slice_error_noalloc", "ttals_create_batch", "ttals_push_batch", "ttals_batch_select",
-           "ttals_batch_size", "ttals_push_batch_masked")
+           "ttals_batch_size", "ttals_push_batch_masked", "ttals_widen_u8")
 
 
 class TTALSError(RuntimeError):
@@ -77,6 +77,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "ttals_push_batch": (ctypes.c_int, [VP, VP, ctypes.c_int, VP]),
         "ttals_batch_select": (ctypes.c_int, [VP, ctypes.c_int]),
         "ttals_push_batch_masked": (ctypes.c_int, [VP, VP, ctypes.c_int, ctypes.c_uint64, VP]),
+        "ttals_widen_u8": (ctypes.c_int, [VP, VP, ctypes.c_int, ctypes.c_int64, VP]),
         "ttals_batch_size": (ctypes.c_int, [VP]),
     }
     for name, (res, args) in sig.items():
@@ -250,6 +251,14 @@ class Stream:
         n = ctypes.c_int64()
         _check(load().ttals_profile_read(self._h, ms, ctypes.byref(n)), "ttals_profile_read")
         return ms[0], ms[1], ms[2], ms[3], n.value
+
+
+def widen_u8(src, dst, stream=None):
+    """ttals_widen_u8: dst (CUDA float16/bfloat16/float32) = src (CUDA uint8), exact."""
+    dt = DTYPES[_TORCH_DTYPES[str(dst.dtype).replace("torch.", "")]]
+    _check(load().ttals_widen_u8(ctypes.c_void_p(src.data_ptr()), ctypes.c_void_p(dst.data_ptr()), dt,
+                                 ctypes.c_int64(src.numel()), ctypes.c_void_p(_stream_handle(stream))),
+           "ttals_widen_u8")
 
 
 _TORCH_DTYPES = {"float64": "f64", "float32": "f32", "float16": "f16", "bfloat16": "bf16"}

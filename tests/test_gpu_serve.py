@@ -121,3 +121,33 @@ def test_serving_budget_queues_then_reuses_slot():
     _close(_served(torch, srv, 1, dims), _alone(torch, dims, srv.key(dims, ranks)[1], 1, frames[1]), 1)
     _close(_served(torch, srv, 2, dims), _alone(torch, dims, srv.key(dims, ranks)[1], 2, frames[2]), 2)
     srv.close()
+
+
+def test_u8_wire_bitwise_equals_f16_wire():
+    """8-bit frames widened on the device (ttals_widen_u8) give bitwise the results of the
+    same frames sent as FP16 (the widening is exact)."""
+    torch = _torch()
+    from paper_2606_31061_b300 import serve
+    from paper_2606_31061_b300.ttals import widen_u8
+    dims, ranks = (96, 128, 3), (20, 10, 3)
+    sp = synth.make_stream("video", dims=dims, seed=4242)
+    raw = [np.clip(np.rint(x), 0, 255).astype(np.uint8) for x in sp.take(3)]
+    u8 = [torch.from_numpy(x).pin_memory() for x in raw]
+    f16 = [torch.from_numpy(x.astype(np.float16)).pin_memory() for x in raw]
+    # the widening itself, with a ragged tail (n % 16 != 0)
+    src = torch.from_numpy(raw[0].reshape(-1)[:1000 - 3].copy()).cuda()
+    for dt in (torch.float16, torch.bfloat16, torch.float32):
+        dst = torch.empty(src.numel(), dtype=dt, device="cuda")
+        widen_u8(src, dst)
+        torch.cuda.synchronize()
+        assert torch.equal(dst.cpu().float(), src.cpu().float()), dt
+    out = []
+    for wire, fr in (("u8", u8), ("f16", f16)):
+        srv = serve.Server(8 << 30, slots=2, rank_step=16, init_cores=_init, wire=wire)
+        assert srv.connect(0, dims, ranks)
+        for f in fr:
+            srv.submit(0, f, 0.0)
+        _drain(srv)
+        out.append(_served(torch, srv, 0, dims))
+        srv.close()
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
