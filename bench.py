@@ -391,10 +391,13 @@ def _serve_frames(nframes=6):
     return pools
 
 
-def serve_arm(seconds=2.0, n=256, lam=30.0, budget=150e9, slots=8):
+def serve_arm(seconds=2.0, n=256, lam=30.0, budget=150e9, slots=8, rank_step=16, quantum=0.002):
     """Continuous-batching serving loop (paper_2606_31061_b300.serve) in real time: n streams,
     Poisson frame arrivals at `lam` frames/s each for `seconds`, admission by an HBM budget.
-    Latency per frame = detection of its step's completion - arrival.  Also: the drain rate
+    Latency per frame = detection of its step's completion - arrival.  Ranks are rounded up
+    to multiples of `rank_step` (pools of many streams) and the loop ticks every `quantum`
+    seconds (several frames per pool step): per-step host cost, not the GPU, bounds a loop
+    that steps one frame at a time.  Also: the drain rate
     with every frame already queued (capacity), and the per-stream FP64 path's capacity
     for the same mix of sizes."""
     import torch
@@ -410,15 +413,20 @@ def serve_arm(seconds=2.0, n=256, lam=30.0, budget=150e9, slots=8):
     events.sort()
 
     def run(evts, realtime):
-        srv = serve.Server(int(budget), slots=slots, rank_step=16, wire="u8")
+        srv = serve.Server(int(budget), slots=slots, rank_step=rank_step, wire="u8")
         admitted = sum(srv.connect(sid, d, r) for sid, (d, r) in enumerate(specs))
         torch.cuda.synchronize()
         nxt = {sid: 0 for sid in range(n)}
         h2d = 0
         t0 = time.perf_counter()
         i = 0
+        last_tick = -1.0
         while i < len(evts) or srv.backlog():
             now = time.perf_counter() - t0
+            if realtime and now - last_tick < quantum:
+                srv.poll()
+                continue
+            last_tick = now
             while i < len(evts) and (not realtime or evts[i][0] <= now):
                 ta, sid = evts[i]
                 d = specs[sid][0]
@@ -438,6 +446,8 @@ def serve_arm(seconds=2.0, n=256, lam=30.0, budget=150e9, slots=8):
         return out
 
     rt = run(events, True)
+    half = [e for j, e in enumerate(events) if j % 2 == 0]     # every other arrival: lam / 2
+    rt_half = run(half, True)
     cap_events = [(0.0, sid) for sid in range(n) for _ in range(4)]
     cap = run(cap_events, False)
     # per-stream FP64 path: one stream per size, device-resident FP64 frames, device-timed
@@ -461,15 +471,19 @@ def serve_arm(seconds=2.0, n=256, lam=30.0, budget=150e9, slots=8):
     lat = rt["latency_s"]
     return {
         "workload": f"{n} streams, sizes in thirds 256x256 / 720x1280x3 / 1080x1920x3, ranks U[8,48] per bond "
-                    f"(rounded up to multiples of 16 for pooling), Poisson arrivals {lam:g} frames/s each for "
+                    f"(rounded up to multiples of {rank_step} for pooling), Poisson arrivals {lam:g} frames/s each for "
                     f"{seconds:g} s, 8-bit frames over the host link widened to FP16 on the device, "
-                    f"HBM budget {budget / 1e9:g} GB, pools of {slots} slots",
+                    f"HBM budget {budget / 1e9:g} GB, pools of {slots} slots, ticks every {quantum * 1e3:g} ms",
         "offered_slices_s": len(events) / seconds,
         "served_slices_s": rt["frames"] / rt["seconds"],
         "latency_ms": {"p50": lat["p50"] * 1e3 if lat["p50"] is not None else None,
                        "p99": lat["p99"] * 1e3 if lat["p99"] is not None else None, "n": lat["n"],
                        "what": "frame arrival -> host detection of its step's completion event"},
-        "realtime": rt, "capacity_slices_s": cap["frames"] / cap["seconds"], "capacity_run": cap,
+        "realtime": rt,
+        "half_load": {"offered_slices_s": len(half) / seconds, "served_slices_s": rt_half["frames"] / rt_half["seconds"],
+                      "latency_ms": {"p50": rt_half["latency_s"]["p50"] * 1e3, "p99": rt_half["latency_s"]["p99"] * 1e3,
+                                     "n": rt_half["latency_s"]["n"]}, "run": rt_half},
+        "capacity_slices_s": cap["frames"] / cap["seconds"], "capacity_run": cap,
         "fp64_plain_per_stream_slices_s": fp64, "fp64_plain_mix_capacity_slices_s": fp64_mix,
         "vs_fp64_plain_capacity": (cap["frames"] / cap["seconds"]) / fp64_mix,
     }

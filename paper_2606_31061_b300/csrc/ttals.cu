@@ -280,8 +280,7 @@ struct Impl final : ttals_stream {
   static constexpr bool kHalfIngest = std::is_same<TX, __half>::value || std::is_same<TX, __nv_bfloat16>::value;
   bool fast = false;
   int np_ = 16;                 // rank padded to a multiple of 16
-  int k1_rows = 0, k1_split = 1, k2_cols = 0, k2_nq = 1, k2_rch = 16;
-  long long k1_kchunk = 64;
+  int k1_rows = 0, k2_cols = 0, k2_nq = 1, k2_rch = 16;
   size_t k1_smem = 0, k2_smem = 0;
   // state slabs [nbatch][...] and views of the selected stream's slab
   float* fQb[2] = {};           // Q1 (I_1 x r)
@@ -412,15 +411,6 @@ struct Impl final : ttals_stream {
       return TTALS_OK;
     }
     k1_rows = (int)cdiv(M, fast::K1_BM);
-    // k-splits of the solve: up to two CTAs per SM over the whole batch, and clusters of 8
-    // only while they fit one CTA per SM (more of them do not all fit the GPCs at once); a
-    // batch that fills the GPU with row tiles takes none (longer CTAs, no cluster reduction)
-    k1_split = 8;
-    while (k1_split > 1 && ((long long)k1_rows * k1_split * nbatch > 2 * kSMs ||
-                            (k1_split == 8 && (long long)k1_rows * k1_split * nbatch > kSMs)))
-      k1_split >>= 1;
-    if (cfg_k1_split > 0) k1_split = cfg_k1_split;
-    k1_kchunk = cdiv(cdiv(J, k1_split), fast::K1_BK) * fast::K1_BK;
     k2_cols = (int)cdiv(J, fast::K2_BN);
     // row chunks per cluster: the fewest (largest chunks) that keep two env CTAs per SM
     auto k2_bytes = [&](int rch) -> size_t {
@@ -507,7 +497,7 @@ struct Impl final : ttals_stream {
     }
     TT_TRY(dalloc(&fShiftb, S * 2));
     TT_TRY(dalloc(&fY, S * M * r));
-    TT_TRY(dalloc(&fXX, S * k1_rows * k1_split));
+    TT_TRY(dalloc(&fXX, S * k1_rows * 8));            // room for the largest k-split
     TT_TRY(dalloc(&fQh, S * M * np_));
     TT_TRY(dalloc(&fW2part, S * fast::KB_CLUSTER * np_ * np_));
     TT_TRY(dalloc(&fQfb, S * M * r));
@@ -571,7 +561,6 @@ struct Impl final : ttals_stream {
       cudaLaunchAttribute at[2];
       at[0].id = cudaLaunchAttributeClusterDimension;
       at[0].val.clusterDim.x = 1;
-      at[0].val.clusterDim.y = (unsigned)k1_split;
       at[0].val.clusterDim.z = 1;
       at[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
       at[1].val.programmaticStreamSerializationAllowed = (profiling || no_pdl) ? 0 : 1;
@@ -585,18 +574,37 @@ struct Impl final : ttals_stream {
       }
       const CUtensorMap& mapX1 = maps[0];
       const CUtensorMap& mapX2 = maps[1];
+      // the grids' planes cover the streams that step; the others' state is carried over
+      unsigned char zact[64], zidle[64];
+      int n_act = 0, n_idle = 0;
+      for (int b = 0; b < nbatch; ++b) {
+        if ((active_mask >> b) & 1ull) zact[n_act++] = (unsigned char)b;
+        else zidle[n_idle++] = (unsigned char)b;
+      }
+      if (n_act == 0) return TTALS_OK;
+      // k-splits of the solve, for the streams that step: up to two CTAs per SM, and clusters
+      // of 8 only while they fit one CTA per SM (more 8-CTA clusters do not fit the GPCs at
+      // once); a batch that fills the GPU with row tiles takes none (longer CTAs, no cluster
+      // reduction).  A configured split wins.
+      int split = 8;
+      while (split > 1 && ((long long)k1_rows * split * n_act > 2 * kSMs ||
+                           (split == 8 && (long long)k1_rows * split * n_act > kSMs)))
+        split >>= 1;
+      if (cfg_k1_split > 0) split = cfg_k1_split;
+      const long long kchunk = cdiv(cdiv(rest[1], split), fast::K1_BK) * fast::K1_BK;
+      at[0].val.clusterDim.y = (unsigned)split;
       // K1: local solve
       fast::SolveArgs a1{};
       a1.M = (int)dims[0];
       a1.r = r;
       a1.K = rest[1];
-      a1.kchunk = k1_kchunk;
+      a1.kchunk = kchunk;
       a1.Y = fY;
       a1.xx_part = fXX;
       a1.ctl = ctl_base;
-      a1.active = active_mask;
+      std::memcpy(a1.zmap, zact, sizeof(zact));
       cudaLaunchConfig_t c1{};
-      c1.gridDim = dim3((unsigned)k1_rows, (unsigned)k1_split, (unsigned)nbatch);
+      c1.gridDim = dim3((unsigned)k1_rows, (unsigned)split, (unsigned)n_act);
       c1.blockDim = dim3(fast::K1_THREADS, 1, 1);
       c1.dynamicSmemBytes = k1_smem;
       c1.stream = s;
@@ -610,7 +618,7 @@ struct Impl final : ttals_stream {
       fast::FactorArgs ab{};
       ab.Y = fY;
       ab.xx_part = fXX;
-      ab.nxx = k1_rows * k1_split;
+      ab.nxx = k1_rows * split;
       ab.M = (int)dims[0];
       ab.r = r;
       ab.Qh = fQh;
@@ -619,13 +627,13 @@ struct Impl final : ttals_stream {
       ab.hh_work = fHH;
       ab.Qfb = fQfb;
       ab.ctl = ctl_base;
-      ab.active = active_mask;
+      std::memcpy(ab.zmap, zact, sizeof(zact));
       cudaLaunchAttribute atb[2];
       atb[0] = at[0];
       atb[0].val.clusterDim.y = (unsigned)fast::KB_CLUSTER;
       atb[1] = at[1];
       cudaLaunchConfig_t cb{};
-      cb.gridDim = dim3(1, (unsigned)fast::KB_CLUSTER, (unsigned)nbatch);
+      cb.gridDim = dim3(1, (unsigned)fast::KB_CLUSTER, (unsigned)n_act);
       cb.blockDim = dim3(fast::K1B_THREADS, 1, 1);
       cb.dynamicSmemBytes = fast::k1b_smem_bytes((int)dims[0], r, NP);
       cb.stream = s;
@@ -656,10 +664,10 @@ struct Impl final : ttals_stream {
       a2.W2old = fW2b[par];
       a2.ch_shift_old = fShiftb + par;
       a2.is_half = std::is_same<TX, __half>::value ? 1 : 0;
-      a2.active = active_mask;
+      std::memcpy(a2.zmap, zact, sizeof(zact));
       at[0].val.clusterDim.y = (unsigned)k2_nq;
       cudaLaunchConfig_t c2{};
-      c2.gridDim = dim3((unsigned)k2_cols, (unsigned)k2_nq, (unsigned)nbatch);
+      c2.gridDim = dim3((unsigned)k2_cols, (unsigned)k2_nq, (unsigned)n_act);
       c2.blockDim = dim3(fast::K2_THREADS, 1, 1);
       c2.dynamicSmemBytes = k2_smem;
       c2.stream = s;
@@ -679,6 +687,16 @@ struct Impl final : ttals_stream {
       }
       ++nlaunch;
       TT_TRY(mark(4, s));
+      if (n_idle > 0) {
+        // streams without a slice this step: their state moves to the new buffers unchanged
+        fast::EnvArgs ac = a2;
+        std::memcpy(ac.zmap, zidle, sizeof(zidle));
+        const long long rj = (long long)r * rest[1];
+        const int nb = (int)std::min<long long>(cdiv(rj, 256), 64);
+        fast::k_fast_carry<TX, NP><<<dim3((unsigned)nb, 1, (unsigned)n_idle), 256, 0, s>>>(ac);
+        TT_CUDA(cudaGetLastError());
+        ++nlaunch;
+      }
       finalized[np] = false;
       materialised = false;
       par = np;

@@ -267,7 +267,7 @@ struct SolveArgs {
   float* Y;               // M x r
   float2* xx_part;        // [row tiles * splits] float-float partials of ||x||^2
   Ctl* ctl;
-  unsigned long long active;   // bit z: stream z of the batch takes this step
+  unsigned char zmap[64];      // grid plane blockIdx.z -> stream (slot) of the batch
 };
 
 template <int NP>
@@ -288,14 +288,9 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
 template <typename TX, int NP>
 __global__ void __launch_bounds__(K1_THREADS, 2)
     k_fast_solve(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmB, SolveArgs a0) {
-  // stream blockIdx.z of a batch: its slice and its B are plane z of the 3-D maps
-  const int zs = blockIdx.z;
-  if (!((a0.active >> zs) & 1ull)) {
-    // a stream without a slice this step: nothing to do, but the wait keeps this grid from
-    // completing before its predecessor (the chain's ordering runs through every CTA)
-    pdl_wait();
-    return;
-  }
+  // grid plane z serves stream zs of the batch (the planes cover the streams that step):
+  // its slice and its B are plane zs of the 3-D maps
+  const int zs = a0.zmap[blockIdx.z];
   SolveArgs a = a0;
   a.Y += (size_t)zs * a.M * a.r;
   a.xx_part += (size_t)zs * gridDim.x * gridDim.y;
@@ -515,7 +510,7 @@ struct FactorArgs {
   double* hh_work;        // 2*M*r doubles (fallback)
   float* Qfb;             // M x r (fallback Q, float)
   Ctl* ctl;
-  unsigned long long active;   // bit z: stream z of the batch takes this step
+  unsigned char zmap[64];      // grid plane blockIdx.z -> stream (slot) of the batch
 };
 
 // rows of Y handled by one CTA of the factor cluster
@@ -533,12 +528,8 @@ __host__ __device__ constexpr size_t k1b_smem_bytes(int M, int r, int np) {
 
 template <typename TX, int NP>
 __global__ void __launch_bounds__(K1B_THREADS, 1) k_fast_factor(FactorArgs a0) {
-  // stream blockIdx.z of a batch: its state and scratch slabs
-  const int zs = blockIdx.z;
-  if (!((a0.active >> zs) & 1ull)) {   // no slice this step (see k_fast_solve)
-    pdl_wait();
-    return;
-  }
+  // grid plane z serves stream zs of the batch: its state and scratch slabs
+  const int zs = a0.zmap[blockIdx.z];
   FactorArgs a = a0;
   a.Y += (size_t)zs * a.M * a.r;
   a.xx_part += (size_t)zs * a.nxx;
@@ -1008,7 +999,7 @@ struct EnvArgs {
   const float* W2old;
   const int* ch_shift_old;
   int is_half;          // 1: FP16 copy needs a range scale; 0: BF16
-  unsigned long long active;   // bit z: stream z of the batch takes this step
+  unsigned char zmap[64];      // grid plane blockIdx.z -> stream (slot) of the batch
 };
 
 template <int NP>
@@ -1046,9 +1037,8 @@ __device__ __forceinline__ EnvArgs env_args_for_stream(const EnvArgs& a0, int z,
 template <typename TX, int NP>
 __global__ void __launch_bounds__(K2_THREADS, 2)
     k_fast_env(const __grid_constant__ CUtensorMap tmX, EnvArgs a0) {
-  const int zs = blockIdx.z;
+  const int zs = a0.zmap[blockIdx.z];     // grid plane z serves stream zs of the batch
   const EnvArgs a = env_args_for_stream<TX, NP>(a0, zs, gridDim.x * gridDim.y);
-  const bool act = (a.active >> zs) & 1ull;   // this stream has a slice this step
   constexpr int NT = NP / 8;   // n8-tiles per warp (each warp covers all NP columns)
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
@@ -1082,11 +1072,9 @@ __global__ void __launch_bounds__(K2_THREADS, 2)
     mbar_fence_init();
     timeout_flag = 0;
     const uint32_t bar = smem_u32(&xbar);
-    if (act) {
-      mbar_arrive_expect_tx(bar, (uint32_t)rch * 256);
-      tma_load_3d(xsub0, &tmX, (int)j0, i0, zs, bar);
-      tma_load_3d(xsub1, &tmX, (int)j0 + 64, i0, zs, bar);
-    }
+    mbar_arrive_expect_tx(bar, (uint32_t)rch * 256);
+    tma_load_3d(xsub0, &tmX, (int)j0, i0, zs, bar);
+    tma_load_3d(xsub1, &tmX, (int)j0 + 64, i0, zs, bar);
   }
   if (tr0) TTRACE(20);
   // 2. wait for the factor kernel (Q1, Nx, ctl)
@@ -1101,8 +1089,8 @@ __global__ void __launch_bounds__(K2_THREADS, 2)
     sum_ee = a.ctl->sum_ee;
     tcount = a.ctl->t;
   }
-  if (!act || a.ctl->skip) {
-    // no slice this step, or a non-finite one: the new state is the old one
+  if (a.ctl->skip) {
+    // non-finite slice: the new state is the old one
     const long long nthr = (long long)gridDim.x * gridDim.y * K2_THREADS;
     const long long me = ((long long)blockIdx.y * gridDim.x + blockIdx.x) * K2_THREADS + tid;
     for (long long e = me; e < (long long)a.M * r; e += nthr) a.Qst[e] = a.Qold[e];
@@ -1112,7 +1100,7 @@ __global__ void __launch_bounds__(K2_THREADS, 2)
     }
     for (long long e = me; e < rr; e += nthr) a.W2st[e] = a.W2old[e];
     if (me == 0) *a.ch_shift = *a.ch_shift_old;
-    if (act && !mbar_wait(smem_u32(&xbar), 0) && tid == 0) a.ctl->latched = 5;
+    if (!mbar_wait(smem_u32(&xbar), 0) && tid == 0) a.ctl->latched = 5;
     return;
   }
   // 3. Q1 rows of this chunk (ingest type) and Nx
@@ -1294,9 +1282,8 @@ __host__ __device__ constexpr bool k2s_fits(int M, int r) {
 template <typename TX, int NP>
 __global__ void __launch_bounds__(K2_THREADS, 1)
     k_fast_env1(const __grid_constant__ CUtensorMap tmX, EnvArgs a0) {
-  const int zs = blockIdx.z;
+  const int zs = a0.zmap[blockIdx.z];     // grid plane z serves stream zs of the batch
   const EnvArgs a = env_args_for_stream<TX, NP>(a0, zs, gridDim.x * gridDim.y);
-  const bool act = (a.active >> zs) & 1ull;   // this stream has a slice this step
   constexpr int NT = NP / 8;          // n8-tiles of the output per warp
   constexpr int MT = K2S_BN / 16;     // m16-tiles (64 columns)
   extern __shared__ unsigned char smem_raw[];
@@ -1332,10 +1319,8 @@ __global__ void __launch_bounds__(K2_THREADS, 1)
     mbar_fence_init();
     timeout_flag = 0;
     const uint32_t bar = smem_u32(&xbar);
-    if (act) {
-      mbar_arrive_expect_tx(bar, (uint32_t)NBX * RB * 128);
-      for (int b = 0; b < NBX; ++b) tma_load_3d(xs + (uint32_t)b * RB * 128, &tmX, (int)j0, b * RB, zs, bar);
-    }
+    mbar_arrive_expect_tx(bar, (uint32_t)NBX * RB * 128);
+    for (int b = 0; b < NBX; ++b) tma_load_3d(xs + (uint32_t)b * RB * 128, &tmX, (int)j0, b * RB, zs, bar);
   }
   if (tr0) TTRACE(20);
   // 2. wait for the factor kernel (Q1, Nx, ctl)
@@ -1350,8 +1335,8 @@ __global__ void __launch_bounds__(K2_THREADS, 1)
     sum_ee = a.ctl->sum_ee;
     tcount = a.ctl->t;
   }
-  if (!act || a.ctl->skip) {
-    // no slice this step, or a non-finite one: the new state is the old one
+  if (a.ctl->skip) {
+    // non-finite slice: the new state is the old one
     const long long nthr = (long long)gridDim.x * K2_THREADS;
     const long long me = (long long)blockIdx.x * K2_THREADS + tid;
     for (long long e = me; e < (long long)M * r; e += nthr) a.Qst[e] = a.Qold[e];
@@ -1361,7 +1346,7 @@ __global__ void __launch_bounds__(K2_THREADS, 1)
     }
     for (long long e = me; e < rr; e += nthr) a.W2st[e] = a.W2old[e];
     if (me == 0) *a.ch_shift = *a.ch_shift_old;
-    if (act && !mbar_wait(smem_u32(&xbar), 0) && tid == 0) a.ctl->latched = 5;
+    if (!mbar_wait(smem_u32(&xbar), 0) && tid == 0) a.ctl->latched = 5;
     return;
   }
   // 3. Q1 (all rows, swizzled; rows past I_1 zero) and Nx
@@ -1518,9 +1503,8 @@ __device__ __forceinline__ void cp_async_mbar_arrive_noinc(uint32_t bar) {
 template <typename TX, int NP>
 __global__ void __launch_bounds__(K2P_THREADS, 2)
     k_fast_env_stream(const __grid_constant__ CUtensorMap tmX, EnvArgs a0) {
-  const int zs = blockIdx.z;
+  const int zs = a0.zmap[blockIdx.z];     // grid plane z serves stream zs of the batch
   const EnvArgs a = env_args_for_stream<TX, NP>(a0, zs, gridDim.x * gridDim.y);
-  const bool act = (a.active >> zs) & 1ull;   // this stream has a slice this step
   constexpr int ST = k2p_stages<NP>();
   static_assert(ST <= K2P_MAXST, "stages");
   constexpr int NT8 = NP / 8;         // n8-tiles of the output (every warp covers all NP)
@@ -1579,7 +1563,7 @@ __global__ void __launch_bounds__(K2P_THREADS, 2)
     timeout_flag = 0;
   }
   __syncthreads();
-  if (act && producer && lane == 0)
+  if (producer && lane == 0)
     for (int t = 0; t < ST && t < nt; ++t) load_x(t, t);
   if (tr0) TTRACE(20);
   // 2. wait for the factor kernel (Q1, W2 partials, ctl)
@@ -1594,8 +1578,8 @@ __global__ void __launch_bounds__(K2P_THREADS, 2)
     sum_ee = a.ctl->sum_ee;
     tcount = a.ctl->t;
   }
-  if (!act || a.ctl->skip) {
-    // no slice this step, or a non-finite one: the new state is the old one
+  if (a.ctl->skip) {
+    // non-finite slice: the new state is the old one
     const long long nthr = (long long)gridDim.x * blockDim.x;
     const long long me = (long long)blockIdx.x * blockDim.x + tid;
     for (long long e = me; e < (long long)M * r; e += nthr) a.Qst[e] = a.Qold[e];
@@ -1605,7 +1589,7 @@ __global__ void __launch_bounds__(K2P_THREADS, 2)
     }
     for (long long e = me; e < rr; e += nthr) a.W2st[e] = a.W2old[e];
     if (me == 0) *a.ch_shift = *a.ch_shift_old;
-    if (act && producer) {
+    if (producer) {
       // the X copies in flight land before the CTA exits: the lanes stand in for the Q1
       // arrivals that never come, then lane 0 waits (bounded) for each stage's phase
       for (int st = 0; st < ST && st < nt; ++st) mbar_arrive(smem_u32(&full[st]));
@@ -1746,6 +1730,26 @@ __global__ void __launch_bounds__(K2P_THREADS, 2)
     c->t = tcount + 1;
   }
   TTRACE(28);
+}
+
+// ================================================================ carry (masked steps)
+// Streams of a batch that take no step this time keep their state: copy it from the old
+// buffers into the new ones (the batch's buffer parity flips for every stream).  Grid plane
+// z serves stream zmap[z]; plain coalesced copies, no dependency on the current step.
+template <typename TX, int NP>
+__global__ void __launch_bounds__(256) k_fast_carry(EnvArgs a0) {
+  const int zs = a0.zmap[blockIdx.z];
+  const EnvArgs a = env_args_for_stream<TX, NP>(a0, zs, 0);
+  const long long nthr = (long long)gridDim.x * blockDim.x;
+  const long long me = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long mr = (long long)a.M * a.r, rj = (long long)a.r * a.J, rr = (long long)a.r * a.r;
+  for (long long e = me; e < mr; e += nthr) a.Qst[e] = a.Qold[e];
+  for (long long e = me; e < rj; e += nthr) {
+    a.Cst[e] = a.Cold[e];
+    ((TX*)a.Chst)[e] = ((const TX*)a.Chold)[e];
+  }
+  for (long long e = me; e < rr; e += nthr) a.W2st[e] = a.W2old[e];
+  if (me == 0) *a.ch_shift = *a.ch_shift_old;
 }
 
 // ------------------------------------------------ helpers for the lazy finalisation

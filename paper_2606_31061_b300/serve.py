@@ -67,7 +67,9 @@ class _Pool:
         self.wire = wire
         self.stage = (torch.zeros((2, self.slots) + self.dims, dtype=torch.uint8, device="cuda")
                       if wire == "u8" else None)
-        self.copy = torch.cuda.Stream()
+        # copies (and the widening of 8-bit frames) run at high priority: a widening kernel
+        # queued behind other pools' compute would hold the host link idle
+        self.copy = torch.cuda.Stream(priority=-5)
         self.comp = torch.cuda.Stream()
         self.copied = [torch.cuda.Event() for _ in range(2)]
         self.consumed = [torch.cuda.Event() for _ in range(2)]
@@ -101,9 +103,12 @@ class _Pool:
                 if self.stage is None:
                     blk[slot].copy_(f, non_blocking=True)
                 else:
-                    from .ttals import widen_u8
                     self.stage[p, slot].copy_(f, non_blocking=True)
-                    widen_u8(self.stage[p, slot], blk[slot], stream=self.copy)
+            if self.stage is not None:
+                # one widening launch for the whole block (slots without a frame this step
+                # are widened too and never read: the masked step skips them)
+                from .ttals import widen_u8
+                widen_u8(self.stage[p], blk, stream=self.copy)
             self.copied[p].record(self.copy)
         self.comp.wait_event(self.copied[p])
         mask = 0
