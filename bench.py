@@ -580,6 +580,25 @@ def run_reference(args, rank):
     print(json.dumps(line), flush=True)
 
 
+def profile_case(args):
+    """Untimed pushes for a profiler capture: one video stream (profile_case = "single") or a
+    batch of args.batch video streams ("batched"), args.warmup + args.steps pushes."""
+    import torch
+    from paper_2606_31061_b300.ttals import Stream
+    S = args.batch if args.profile_case == "batched" else 0
+    pool = to_device(make_pool(args.ingest, max(8, S + 4)), args.ingest)
+    st = Stream(DIMS, RANKS, ingest=args.ingest, n_streams=S)
+    h = torch.cuda.current_stream().cuda_stream
+    for t in range(args.warmup + args.steps):
+        if S:
+            st.push_batch_ptr(pool[t % 4].data_ptr(), h)
+        else:
+            st.push_ptr(pool[t % 8].data_ptr(), h)
+    torch.cuda.synchronize()
+    st.sync()
+    st.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -595,6 +614,9 @@ def main():
     ap.add_argument("--batch-steps", type=int, default=400)
     ap.add_argument("--c4-steps", type=int, default=200, help="mixed-shape group steps (0: skip)")
     ap.add_argument("--serve-seconds", type=float, default=2.0, help="serving-loop traffic (0: skip)")
+    ap.add_argument("--profile-case", default=None, choices=["single", "batched"],
+                    help="for profilers: run --warmup + --steps pushes of one video stream, or of a "
+                         "batch of --batch video streams, untimed, and print no bench line")
     args = ap.parse_args()
     rank = env_int("RANK", 0)
     world = env_int("WORLD_SIZE", 1)
@@ -613,6 +635,9 @@ def main():
     from paper_2606_31061_b300 import build
     if rank == 0 or not dist_on:
         build.build()
+    if args.profile_case:
+        profile_case(args)
+        return
     if dist_on:
         torch.distributed.barrier()
     pool_np = make_pool(args.ingest, args.pool)
