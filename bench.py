@@ -132,8 +132,9 @@ def to_device(pool_np, ingest):
     return t.cuda()
 
 
-def traffic_record(kernel):
-    """DRAM bytes per launch from a committed ncu capture, if the kernel sources are unchanged."""
+def traffic_record(kernel, sub=None):
+    """DRAM bytes per launch from a committed ncu capture, if the kernel sources are unchanged
+    (`sub`: the kernel within a batched record)."""
     try:
         import hashlib
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
@@ -145,7 +146,7 @@ def traffic_record(kernel):
                 h.update(open(os.path.join(src, name), "rb").read())
         r = rec.get(kernel)
         if r and r.get("src_sha256") == h.hexdigest():
-            return r.get("bytes_per_launch")
+            return r["kernel_bytes_per_launch"].get(sub) if sub else r.get("bytes_per_launch")
     except Exception:
         pass
     return None
@@ -697,6 +698,8 @@ def main():
             "re_per_stream": {"min": min(rb["re"]), "max": max(rb["re"])},
             "roofline": {"bound": "hbm", "kernel": bdom, "achieved": bach[bdom], "peak": peak,
                          "peak_source": peak_src, "unit": "GB/s", "frac": bach[bdom] / peak,
+                         "traffic": traffic_record("batched16", {"solve": "solve", "env": "env_stream",
+                                                                 "factor": "factor"}[bdom]) if S == 16 else None,
                          "algorithmic_bytes": S * alg[bdom], "ms_per_launch": bper[bdom],
                          "achieved_all": bach, "ms_per_launch_all": bper},
             "inputs": f"stream b at step t reads pool frame o_t + b; one push reads {S * slice_bytes / 1e6:.0f} MB",
