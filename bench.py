@@ -490,6 +490,73 @@ def serve_arm(seconds=2.0, n=256, lam=30.0, budget=150e9, slots=8, rank_step=16,
     }
 
 
+PAPER_TABLE1_MS = {5: 15.21, 6: 545.5, 7: 17365.0}   # Online TT-ALS, ms per frame (their hardware)
+
+
+def _tt_frames_gpu(dims, gen_rank, nframes, seed, decay=0.7, noise=1e-3):
+    """Synthetic high-order frames built on the device (input generation only): a TT of
+    ground-truth rank `gen_rank` whose cores have decaying column scales (decaying singular
+    values of every unfolding), temporal weights drifting slowly, plus Gaussian noise."""
+    import torch
+    g = torch.Generator(device="cuda").manual_seed(seed)
+    m = len(dims)
+    scale = decay ** torch.arange(gen_rank, device="cuda", dtype=torch.float64)
+    cores = []
+    for k in range(m):
+        a = 1 if k == 0 else gen_rank
+        c = torch.randn((a, dims[k], gen_rank), generator=g, device="cuda", dtype=torch.float64) / math.sqrt(a * dims[k])
+        cores.append(c * scale)
+    w = torch.randn(gen_rank, generator=g, device="cuda", dtype=torch.float64)
+    frames = []
+    for t in range(nframes):
+        w = 0.98 * w + 0.2 * torch.randn(gen_rank, generator=g, device="cuda", dtype=torch.float64)
+        v = torch.tensordot(cores[-1], w, dims=([2], [0]))              # (r, I_m)
+        for k in range(m - 2, -1, -1):
+            v = torch.tensordot(cores[k], v, dims=([2], [0]))           # (a, I_k, ...)
+        x = v.reshape(tuple(dims)).float()
+        x = x / x.std()
+        x += noise * torch.randn(x.shape, generator=g, device="cuda", dtype=torch.float32)
+        frames.append(x.contiguous())
+        del v
+    return frames
+
+
+def table1_arm(orders=(5, 6, 7), I=30, rank=8, steps=6):
+    """Table-1-shaped scalability workload: slices of order n - 1 with I = 30 per mode, TT
+    ranks `rank` on every bond (an assumption: the paper does not state them), FP32 ingest.
+    ms per slice from CUDA events over `steps` pushes after two warm-up pushes."""
+    import torch
+    from paper_2606_31061_b300.ttals import Stream
+    out = {}
+    for n in orders:
+        dims = (I,) * (n - 1)
+        frames = _tt_frames_gpu(dims, rank, 4, seed=659 + n)
+        st = Stream(dims, (rank,) * (n - 1), ingest="f32")
+        for t in range(2):
+            st.push(frames[t % 4])
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for t in range(steps):
+            st.push(frames[t % 4])
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        s_ = st.stats()
+        nbytes = frames[0].numel() * 4
+        out[f"n={n}"] = {"slice_elems": frames[0].numel(), "ms_per_slice": ms, "slices_s": 1000.0 / ms,
+                         "slice_gbs": nbytes / (ms * 1e-3) / 1e9, "re": math.sqrt(s_[3] / s_[2]),
+                         "paper_online_ttals_ms_per_frame": PAPER_TABLE1_MS.get(n),
+                         "device_gb": st.device_bytes / 1e9}
+        st.close()
+        del frames
+        torch.cuda.empty_cache()
+    return {"workload": f"orders n = {orders}, I = {I} per mode, TT ranks {rank} on every bond (assumed), "
+                        "synthetic TT fields with decaying singular values + noise 1e-3, FP32 ingest",
+            "results": out,
+            "paper_note": "the paper's times are on its own hardware: context, not a target"}
+
+
 def e2e_arm(ingest, steps, pool_np, dist_on):
     """Same metric through the C ABI from pinned HOST buffers: per step an H2D copy of the
     slice (copy stream, double-buffered device slot), the push, and an async D2H read of
@@ -615,6 +682,7 @@ def main():
     ap.add_argument("--batch-steps", type=int, default=400)
     ap.add_argument("--c4-steps", type=int, default=200, help="mixed-shape group steps (0: skip)")
     ap.add_argument("--serve-seconds", type=float, default=2.0, help="serving-loop traffic (0: skip)")
+    ap.add_argument("--table1", type=int, default=1, help="high-order scalability arm (0: skip)")
     ap.add_argument("--profile-case", default=None, choices=["single", "batched"],
                     help="for profilers: run --warmup + --steps pushes of one video stream, or of a "
                          "batch of --batch video streams, untimed, and print no bench line")
@@ -706,6 +774,7 @@ def main():
         }
     c4 = c4_arm(args.c4_steps) if args.c4_steps > 0 else None
     served = serve_arm(args.serve_seconds) if args.serve_seconds > 0 and world == 1 else None
+    table1 = table1_arm() if args.table1 and world == 1 else None
     f32 = None
     if not args.no_f32 and args.ingest != "f32":
         del pool
@@ -754,6 +823,7 @@ def main():
             "batched": batched,
             "c4_mixed_shapes": c4,
             "serving": served,
+            "table1_high_order": table1,
             "f32_ingest": f32,
             "cpu_baseline": cpu,
         }

@@ -152,6 +152,15 @@ def test_ragged_shapes(dims, ranks, ingest):
     check(xg, xo, ex, ingest)
 
 
+@pytest.mark.parametrize("ingest", ["f64", "f32"])
+@pytest.mark.parametrize("dims,ranks", [((5, 5, 5, 5, 5), (4, 4, 4, 4, 4)), ((4, 4, 4, 4, 4, 4), (3, 3, 3, 3, 3, 3))])
+def test_high_order_shapes(dims, ranks, ingest):
+    """Orders n = 6 and 7 (the Table-1 orders) at small mode sizes: a drifting low-rank TT."""
+    sp = synth.make_stream("plain", dims=dims, ranks=ranks, gen_ranks=ranks, seed=659 + len(dims))
+    xg, xo, ex, st = run_pair(dims, ranks, sp.take(8), ingest)
+    check(xg, xo, ex, ingest)
+
+
 def test_video_full_size_prefix():
     """The 1080x1920x3 video stream at full size, FP32 and FP16 ingest, first frames."""
     sp = synth.make_stream("video")
