@@ -305,6 +305,8 @@ struct Impl final : ttals_stream {
   // 64-column tiles with the rows streamed through a pipeline
   enum { K2_CLUSTER = 0, K2_SINGLE = 1, K2_STREAM = 2 };
   int k2_kind = K2_CLUSTER;
+  // local solve kernel: mma.sync with k-splits in clusters, or tcgen05 over whole rows
+  bool k1_tc = false;
   unsigned* fCounter = nullptr; // [nbatch][2]
   CUtensorMap mapB[2];          // TMA maps of fChb[p] (nbatch x r x rest_1, box 64 x NP)
 
@@ -389,6 +391,7 @@ struct Impl final : ttals_stream {
   ttals_status set_fast_attrs() {
     if constexpr (kHalfIngest) {
       TT_TRY(raise_smem_limit(fast::k_fast_solve<TX, NP>));
+      TT_TRY(raise_smem_limit(fast::k_fast_solve_tc<TX, NP>));
       TT_TRY(raise_smem_limit(fast::k_fast_env1<TX, NP>));
       TT_TRY(raise_smem_limit(fast::k_fast_env_stream<TX, NP>));
       TT_TRY(raise_smem_limit(fast::k_fast_env<TX, NP>));
@@ -451,6 +454,9 @@ struct Impl final : ttals_stream {
         else if (v == "stream") k2_kind = K2_STREAM;
         else if (v == "single" && fits) k2_kind = K2_SINGLE;
       }
+      // the tcgen05 solve for batches (TTALS_SOLVE_KERNEL=tc|mma overrides)
+      k1_tc = nbatch > 1;
+      if (const char* e = std::getenv("TTALS_SOLVE_KERNEL")) k1_tc = std::string(e) == "tc";
       if (cfg_env_kernel == 1) k2_kind = K2_CLUSTER;          // the stream's config wins
       else if (cfg_env_kernel == 2 && fits) k2_kind = K2_SINGLE;
       else if (cfg_env_kernel == 3) k2_kind = K2_STREAM;
@@ -537,7 +543,7 @@ struct Impl final : ttals_stream {
 
   // per-slice-address TMA maps {solve box, env box}; cleared when it reaches its cap
   struct SliceMaps {
-    CUtensorMap m[2];
+    CUtensorMap m[3];           // solve box 64 x 64, env box 64 x rch, tcgen05 solve box 64 x 128
   };
   std::unordered_map<const void*, SliceMaps> map_cache;
   const CUtensorMap* slice_maps(const TX* X) {
@@ -548,7 +554,8 @@ struct Impl final : ttals_stream {
     SliceMaps sm;
     const bool bf = std::is_same<TX, __nv_bfloat16>::value;
     if (!encode_map_3d(&sm.m[0], X, bf, nbatch, dims[0], rest[1], fast::K1_BM) ||
-        !encode_map_3d(&sm.m[1], X, bf, nbatch, dims[0], rest[1], k2_rch))
+        !encode_map_3d(&sm.m[1], X, bf, nbatch, dims[0], rest[1], k2_rch) ||
+        !encode_map_3d(&sm.m[2], X, bf, nbatch, dims[0], rest[1], fast::K1T_BM))
       return nullptr;
     return map_cache.emplace((const void*)X, sm).first->second.m;
   }
@@ -611,14 +618,26 @@ struct Impl final : ttals_stream {
       c1.attrs = at;
       c1.numAttrs = 2;
       TT_TRY(mark(1, s));
-      TT_CUDA(cudaLaunchKernelEx(&c1, fast::k_fast_solve<TX, NP>, mapX1, mapB[par], a1));
+      int nxx = k1_rows * split;               // ||x||^2 partials per stream
+      if (k1_tc) {
+        const int rows_tc = (int)cdiv(dims[0], fast::K1T_BM);
+        c1.gridDim = dim3((unsigned)rows_tc, 1, (unsigned)n_act);
+        c1.blockDim = dim3(fast::K1T_THREADS, 1, 1);
+        c1.dynamicSmemBytes = fast::k1t_smem_bytes<NP>();
+        c1.attrs = at + 1;                     // no cluster
+        c1.numAttrs = 1;
+        TT_CUDA(cudaLaunchKernelEx(&c1, fast::k_fast_solve_tc<TX, NP>, maps[2], mapB[par], a1));
+        nxx = rows_tc;
+      } else {
+        TT_CUDA(cudaLaunchKernelEx(&c1, fast::k_fast_solve<TX, NP>, mapX1, mapB[par], a1));
+      }
       ++nlaunch;
       TT_TRY(mark(2, s));
       // K1b: r x r factor, Q1, W2, Nx
       fast::FactorArgs ab{};
       ab.Y = fY;
       ab.xx_part = fXX;
-      ab.nxx = k1_rows * split;
+      ab.nxx = nxx;
       ab.M = (int)dims[0];
       ab.r = r;
       ab.Qh = fQh;

@@ -486,6 +486,281 @@ __global__ void __launch_bounds__(K1_THREADS, 2)
   if (tr0) TTRACE(3);
 }
 
+// ================================================================ K1 on tcgen05 (batches)
+// Y = X_(1) B^T for one 128-row tile of X over all of rest_1 (no k-split), on the 5th-gen
+// tensor cores: warp 0 issues the TMA copies (stages of two 64-column boxes of X, 128 rows,
+// and of B, NP rows: 256 contiguous bytes of every row per stage); warp 1's elected lane
+// issues tcgen05.mma (M = 128, N = NP, K = 16 per instruction, FP32 accumulator in TMEM;
+// operands through SWIZZLE_128B K-major shared-memory descriptors) and frees each stage with
+// tcgen05.commit; warps 2-5 form ||x||^2 from the staged X tiles, release the stage, and at
+// the end read the accumulator (tcgen05.ld, one TMEM lane = one row of Y) and write Y.
+// The stage is free when the MMAs that read it have completed and the four ||x||^2 warps
+// have read it (its `empty` barrier counts 1 + 4 arrivals).
+constexpr int K1T_BM = 128;
+constexpr int K1T_THREADS = 192;
+constexpr int K1T_MAXST = 5;
+template <int NP>
+__host__ __device__ constexpr int k1t_stages() { return NP <= 32 ? 5 : 4; }
+template <int NP>
+__host__ __device__ constexpr size_t k1t_stage_bytes() { return (size_t)(K1T_BM + NP) * 256; }
+template <int NP>
+__host__ __device__ constexpr size_t k1t_smem_bytes() {
+  return (size_t)k1t_stages<NP>() * k1t_stage_bytes<NP>() + 1024;
+}
+
+// shared-memory matrix descriptor: K-major operand, 128B swizzle, 8-row groups 1024 B apart
+__device__ __forceinline__ uint64_t umma_desc_sw128(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFFu);          // start address (16-byte units)
+  d |= (uint64_t)1u << 16;                          // leading byte offset (unused when swizzled)
+  d |= (uint64_t)(1024u >> 4) << 32;                // stride byte offset: 8 rows x 128 B
+  d |= (uint64_t)1u << 46;                          // descriptor version (sm_100 family)
+  d |= (uint64_t)2u << 61;                          // layout: 128-byte swizzle
+  return d;
+}
+// instruction descriptor, kind::f16: FP32 accumulator, A and B of the ingest type, both K-major
+template <typename TX>
+__host__ __device__ constexpr uint32_t umma_idesc_f16(int M, int N) {
+  return (1u << 4) | ((std::is_same<TX, __nv_bfloat16>::value ? 1u : 0u) << 7) |
+         ((std::is_same<TX, __nv_bfloat16>::value ? 1u : 0u) << 10) | ((uint32_t)(N >> 3) << 17) |
+         ((uint32_t)(M >> 4) << 24);
+}
+__device__ __forceinline__ void umma_f16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+__device__ __forceinline__ void umma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(bar)
+               : "memory");
+}
+__device__ __forceinline__ void tmem_alloc(uint32_t holder, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(holder), "r"(ncols)
+               : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(taddr), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory"); }
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+}
+// 32 consecutive FP32 columns of this warp's 32 TMEM lanes (lane = thread)
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+template <typename TX, int NP>
+__global__ void __launch_bounds__(K1T_THREADS, 1)
+    k_fast_solve_tc(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmB, SolveArgs a0) {
+  const int zs = a0.zmap[blockIdx.z];   // grid plane z serves stream zs of the batch
+  SolveArgs a = a0;
+  a.Y += (size_t)zs * a.M * a.r;
+  a.xx_part += (size_t)zs * gridDim.x;
+  a.ctl += zs;
+  static_assert(NP % 16 == 0 && NP >= 16 && NP <= 64, "NP");
+  constexpr int ST = k1t_stages<NP>();
+  static_assert(ST <= K1T_MAXST, "stages");
+  constexpr uint32_t ABOX = K1T_BM * 128, BBOX = NP * 128;     // one 64-column box of X / of B
+  constexpr uint32_t ABYTES = 2 * ABOX, BBYTES = 2 * BBOX;
+  constexpr uint32_t TCOLS = NP <= 32 ? 32 : 64;               // TMEM columns (power of 2 >= 32)
+  constexpr uint32_t IDESC = umma_idesc_f16<TX>(K1T_BM, NP);
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+  __shared__ __align__(8) uint64_t full[K1T_MAXST];
+  __shared__ __align__(8) uint64_t empty[K1T_MAXST];
+  __shared__ __align__(8) uint64_t done;
+  __shared__ uint32_t tmem_holder;
+  __shared__ float redf[64];
+  __shared__ int timeout_flag;
+
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int rt = blockIdx.x;
+  const int m0 = rt * K1T_BM;
+  const int r = a.r;
+  const long long K = a.K;
+  const int ntk = (int)((K + 127) / 128);
+  const uint32_t sbase = smem_u32(smem);
+  auto stageA = [&](int st) { return sbase + (uint32_t)(st * k1t_stage_bytes<NP>()); };
+  auto stageB = [&](int st) { return stageA(st) + ABYTES; };
+
+  if (tid == 0) {
+    for (int s = 0; s < ST; ++s) {
+      mbar_init(smem_u32(&full[s]), 2);          // A arrival + B arrival (expect_tx)
+      mbar_init(smem_u32(&empty[s]), 1 + 4);     // MMA commit + the four ||x||^2 warps
+    }
+    mbar_init(smem_u32(&done), 1);
+    mbar_fence_init();
+    timeout_flag = 0;
+  }
+  if (warp == 1) tmem_alloc(smem_u32(&tmem_holder), TCOLS);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_holder;
+  // X tiles do not depend on the previous kernel: start them before the dependency wait
+  if (warp == 0 && lane == 0) {
+    for (int t = 0; t < ST && t < ntk; ++t) {
+      mbar_arrive_expect_tx(smem_u32(&full[t]), ABYTES);
+      const int x = t * 128;
+      tma_load_3d(stageA(t), &tmX, x, m0, zs, smem_u32(&full[t]));
+      tma_load_3d(stageA(t) + ABOX, &tmX, x + 64, m0, zs, smem_u32(&full[t]));
+    }
+  }
+  pdl_wait();       // the previous step's env kernel wrote B and ctl
+  pdl_trigger();
+  const bool bzero = (a.ctl->cc == 0.0);
+  if (bzero) {
+    // e_1 rule for a zero temporal row: B stays zero but for B[0][0] of the first stage
+    for (int st = 0; st < ST; ++st)
+      for (int e = tid; e < (int)BBYTES / 16; e += K1T_THREADS)
+        *reinterpret_cast<uint4*>(smem + (stageB(st) - sbase) + e * 16) = make_uint4(0, 0, 0, 0);
+    fence_proxy_async_smem();                  // each thread's writes, before the MMAs read them
+    __syncthreads();
+    if (tid == 0) {
+      *reinterpret_cast<TX*>(smem + (stageB(0) - sbase)) = from_acc<TX>(1.0f);
+      fence_proxy_async_smem();
+    }
+  }
+  __syncthreads();
+
+  float ssh = 0.f, ssl = 0.f;
+  if (warp == 0) {
+    // ---- producer
+    if (lane == 0) {
+      int issued = ntk < ST ? ntk : ST;
+      for (int t = 0; t < issued; ++t) {
+        if (bzero) {
+          mbar_arrive_expect_tx(smem_u32(&full[t]), 0);
+        } else {
+          mbar_arrive_expect_tx(smem_u32(&full[t]), BBYTES);
+          tma_load_3d(stageB(t), &tmB, t * 128, 0, zs, smem_u32(&full[t]));
+          tma_load_3d(stageB(t) + BBOX, &tmB, t * 128 + 64, 0, zs, smem_u32(&full[t]));
+        }
+      }
+      for (int t = ST; t < ntk; ++t) {
+        const int st = t % ST;
+        if (!mbar_wait(smem_u32(&empty[st]), (uint32_t)(((t / ST) - 1) & 1)) || timeout_flag) {
+          timeout_flag = 1;
+          break;
+        }
+        if (t == ST && bzero) {
+          *reinterpret_cast<TX*>(smem + (stageB(0) - sbase)) = from_acc<TX>(0.f);
+          fence_proxy_async_smem();
+        }
+        const int x = t * 128;
+        mbar_arrive_expect_tx(smem_u32(&full[st]), ABYTES);
+        tma_load_3d(stageA(st), &tmX, x, m0, zs, smem_u32(&full[st]));
+        tma_load_3d(stageA(st) + ABOX, &tmX, x + 64, m0, zs, smem_u32(&full[st]));
+        if (bzero) {
+          mbar_arrive_expect_tx(smem_u32(&full[st]), 0);
+        } else {
+          mbar_arrive_expect_tx(smem_u32(&full[st]), BBYTES);
+          tma_load_3d(stageB(st), &tmB, x, 0, zs, smem_u32(&full[st]));
+          tma_load_3d(stageB(st) + BBOX, &tmB, x + 64, 0, zs, smem_u32(&full[st]));
+        }
+        issued = t + 1;
+      }
+      if (timeout_flag) {
+        for (int t = issued - ST > 0 ? issued - ST : 0; t < issued; ++t)
+          mbar_wait(smem_u32(&full[t % ST]), (uint32_t)((t / ST) & 1));
+      }
+    }
+  } else if (warp == 1) {
+    // ---- MMA issuer
+    int t = 0;
+    if (lane == 0) {
+      for (; t < ntk; ++t) {
+        const int st = t % ST;
+        if (!mbar_wait(smem_u32(&full[st]), (uint32_t)((t / ST) & 1)) || timeout_flag) {
+          timeout_flag = 1;
+          break;
+        }
+        tc_fence_after();
+#pragma unroll
+        for (int bx = 0; bx < 2; ++bx) {
+#pragma unroll
+          for (int kk = 0; kk < 4; ++kk) {
+            const uint64_t ad = umma_desc_sw128(stageA(st) + bx * ABOX + kk * 32);
+            const uint64_t bd = umma_desc_sw128(stageB(st) + bx * BBOX + kk * 32);
+            umma_f16(tmem, ad, bd, IDESC, (t | bx | kk) != 0 ? 1u : 0u);
+          }
+        }
+        umma_commit(smem_u32(&empty[st]));     // the stage is free once these MMAs completed
+      }
+      umma_commit(smem_u32(&done));            // every MMA issued above has completed
+    }
+    __syncwarp();
+  } else {
+    // ---- ||x||^2 of the staged X tiles (thread = row of the tile)
+    const int row = tid - 64;                  // 0..127
+    for (int t = 0; t < ntk; ++t) {
+      const int st = t % ST;
+      if (!mbar_wait(smem_u32(&full[st]), (uint32_t)((t / ST) & 1)) || timeout_flag) {
+        timeout_flag = 1;
+        break;
+      }
+      float ss = 0.f;
+#pragma unroll
+      for (int bx = 0; bx < 2; ++bx) {
+        const unsigned char* rp = smem + (stageA(st) - sbase) + bx * ABOX + row * 128;
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+          const uint4 v = *reinterpret_cast<const uint4*>(rp + c * 16);
+          ss += frag_sumsq<TX>(reinterpret_cast<const uint32_t*>(&v));
+        }
+      }
+      two_sum_acc(ssh, ssl, ss);
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(&empty[st]));
+    }
+  }
+  // ---- epilogue: the accumulator -> Y (warps 2-5: TMEM lanes 32 (warp % 4) ..)
+  if (warp >= 2) {
+    const bool ok = mbar_wait(smem_u32(&done), 0);
+    if (!ok) timeout_flag = 1;
+    tc_fence_after();
+    const int q = warp & 3;                    // TMEM lane quarter of this warp
+    const int row = q * 32 + lane;
+    const int grow = m0 + row;
+    float v[32];
+#pragma unroll
+    for (int c0 = 0; c0 < NP; c0 += 32) {
+      tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, v);
+      if (ok && grow < a.M) {
+#pragma unroll
+        for (int j = 0; j < 32; ++j)
+          if (c0 + j < r) a.Y[(long long)grow * r + c0 + j] = v[j];
+      }
+    }
+  }
+  tc_fence_before();
+  const float2 ss_cta = ff_block_sum(ssh, ssl, redf);   // (includes a block barrier)
+  if (tid == 0) {
+    a.xx_part[rt] = ss_cta;                   // one partial of ||x||^2 per row tile
+    if (timeout_flag) a.ctl->latched = 5;
+  }
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 1) tmem_dealloc(tmem, TCOLS);
+}
+
 // ================================================================ K1b: r x r factor
 // A cluster of KB_CLUSTER CTAs; CTA q owns rows [q*nrows, (q+1)*nrows) of Y.
 //  1. Gram partial of my rows (FP32, 4 x 4 register blocks), W1 = the ranks' partials
