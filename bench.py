@@ -678,7 +678,7 @@ def main():
     ap.add_argument("--no-f32", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=300)
-    ap.add_argument("--batch", type=int, default=16, help="streams per batched push (0: skip)")
+    ap.add_argument("--batch", type=int, default=32, help="streams per batched push (0: skip)")
     ap.add_argument("--batch-steps", type=int, default=400)
     ap.add_argument("--c4-steps", type=int, default=200, help="mixed-shape group steps (0: skip)")
     ap.add_argument("--serve-seconds", type=float, default=2.0, help="serving-loop traffic (0: skip)")
@@ -766,8 +766,8 @@ def main():
             "re_per_stream": {"min": min(rb["re"]), "max": max(rb["re"])},
             "roofline": {"bound": "hbm", "kernel": bdom, "achieved": bach[bdom], "peak": peak,
                          "peak_source": peak_src, "unit": "GB/s", "frac": bach[bdom] / peak,
-                         "traffic": traffic_record("batched16", {"solve": "solve", "env": "env_stream",
-                                                                 "factor": "factor"}[bdom]) if S == 16 else None,
+                         "traffic": traffic_record(f"batched{S}", {"solve": "solve", "env": "env_stream",
+                                                                   "factor": "factor"}[bdom]),
                          "algorithmic_bytes": S * alg[bdom], "ms_per_launch": bper[bdom],
                          "achieved_all": bach, "ms_per_launch_all": bper},
             "inputs": f"stream b at step t reads pool frame o_t + b; one push reads {S * slice_bytes / 1e6:.0f} MB",

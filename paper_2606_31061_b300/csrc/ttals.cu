@@ -306,7 +306,8 @@ struct Impl final : ttals_stream {
   enum { K2_CLUSTER = 0, K2_SINGLE = 1, K2_STREAM = 2 };
   int k2_kind = K2_CLUSTER;
   // local solve kernel: mma.sync with k-splits in clusters, or tcgen05 over whole rows
-  bool k1_tc = false;
+  // (0: chosen per launch, 1: always tcgen05, -1: never)
+  int k1_tc = 0;
   unsigned* fCounter = nullptr; // [nbatch][2]
   CUtensorMap mapB[2];          // TMA maps of fChb[p] (nbatch x r x rest_1, box 64 x NP)
 
@@ -454,9 +455,8 @@ struct Impl final : ttals_stream {
         else if (v == "stream") k2_kind = K2_STREAM;
         else if (v == "single" && fits) k2_kind = K2_SINGLE;
       }
-      // the tcgen05 solve for batches (TTALS_SOLVE_KERNEL=tc|mma overrides)
-      k1_tc = nbatch > 1;
-      if (const char* e = std::getenv("TTALS_SOLVE_KERNEL")) k1_tc = std::string(e) == "tc";
+      // TTALS_SOLVE_KERNEL=tc|mma fixes the local-solve kernel (else chosen per launch)
+      if (const char* e = std::getenv("TTALS_SOLVE_KERNEL")) k1_tc = std::string(e) == "tc" ? 1 : -1;
       if (cfg_env_kernel == 1) k2_kind = K2_CLUSTER;          // the stream's config wins
       else if (cfg_env_kernel == 2 && fits) k2_kind = K2_SINGLE;
       else if (cfg_env_kernel == 3) k2_kind = K2_STREAM;
@@ -619,8 +619,12 @@ struct Impl final : ttals_stream {
       c1.numAttrs = 2;
       TT_TRY(mark(1, s));
       int nxx = k1_rows * split;               // ||x||^2 partials per stream
-      if (k1_tc) {
-        const int rows_tc = (int)cdiv(dims[0], fast::K1T_BM);
+      // tcgen05 over whole rows once its 128-row tiles of the stepping streams cover three
+      // quarters of the SMs (one CTA per SM); below that the k-split mma.sync kernel fills
+      // the GPU better
+      const int rows_tc = (int)cdiv(dims[0], fast::K1T_BM);
+      const bool use_tc = k1_tc > 0 || (k1_tc == 0 && 4LL * rows_tc * n_act >= 3LL * kSMs);
+      if (use_tc) {
         c1.gridDim = dim3((unsigned)rows_tc, 1, (unsigned)n_act);
         c1.blockDim = dim3(fast::K1T_THREADS, 1, 1);
         c1.dynamicSmemBytes = fast::k1t_smem_bytes<NP>();

@@ -566,6 +566,13 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
   for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// the two 16-bit values packed in w, widened to FP32
+template <typename TX>
+__device__ __forceinline__ float2 sq_pair(uint32_t w) {
+  if constexpr (std::is_same<TX, __half>::value) return __half22float2(*reinterpret_cast<const __half2*>(&w));
+  else return __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&w));
+}
+
 template <typename TX, int NP>
 __global__ void __launch_bounds__(K1T_THREADS, 1)
     k_fast_solve_tc(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmB, SolveArgs a0) {
@@ -716,16 +723,32 @@ __global__ void __launch_bounds__(K1T_THREADS, 1)
         timeout_flag = 1;
         break;
       }
-      float ss = 0.f;
+      // shared-memory loads on 32-bit shared addresses, chunk c of the row read where the
+      // 128-byte swizzle put it (c ^ row % 8: the 8 rows of a quarter-warp hit 8 different
+      // bank groups; the unswizzled offset made every lane of a warp hit the same ones), eight
+      // independent accumulators, summed in a fixed order
+      float q0 = 0.f, q1 = 0.f, q2 = 0.f, q3 = 0.f, q4 = 0.f, q5 = 0.f, q6 = 0.f, q7 = 0.f;
 #pragma unroll
       for (int bx = 0; bx < 2; ++bx) {
-        const unsigned char* rp = smem + (stageA(st) - sbase) + bx * ABOX + row * 128;
+        const uint32_t rp = stageA(st) + (uint32_t)(bx * ABOX + row * 128);
 #pragma unroll
         for (int c = 0; c < 8; ++c) {
-          const uint4 v = *reinterpret_cast<const uint4*>(rp + c * 16);
-          ss += frag_sumsq<TX>(reinterpret_cast<const uint32_t*>(&v));
+          uint32_t w0, w1, w2, w3;
+          asm volatile("ld.shared.v4.u32 {%0,%1,%2,%3}, [%4];\n"
+                       : "=r"(w0), "=r"(w1), "=r"(w2), "=r"(w3)
+                       : "r"(rp + (uint32_t)((c ^ (row & 7)) * 16)));
+          const float2 f0 = sq_pair<TX>(w0), f1 = sq_pair<TX>(w1), f2 = sq_pair<TX>(w2), f3 = sq_pair<TX>(w3);
+          q0 = fmaf(f0.x, f0.x, q0);
+          q1 = fmaf(f0.y, f0.y, q1);
+          q2 = fmaf(f1.x, f1.x, q2);
+          q3 = fmaf(f1.y, f1.y, q3);
+          q4 = fmaf(f2.x, f2.x, q4);
+          q5 = fmaf(f2.y, f2.y, q5);
+          q6 = fmaf(f3.x, f3.x, q6);
+          q7 = fmaf(f3.y, f3.y, q7);
         }
       }
+      const float ss = ((q0 + q1) + (q2 + q3)) + ((q4 + q5) + (q6 + q7));
       two_sum_acc(ssh, ssl, ss);
       __syncwarp();
       if (lane == 0) mbar_arrive(smem_u32(&empty[st]));

@@ -140,3 +140,41 @@ def test_batch_argument_errors():
     bt.push_batch(x)
     bt.sync()
     bt.close()
+
+
+def test_batch_tcgen05_solve_matches_alone(monkeypatch):
+    """The tcgen05 local solve (forced for a small batch through TTALS_SOLVE_KERNEL, read when
+    a stream is created) against the same streams alone on the mma.sync kernel."""
+    torch = _torch()
+    monkeypatch.setenv("TTALS_SOLVE_KERNEL", "tc")
+    for name, kw in (("video", {"dims": (96, 128, 3)}), ("square", {"s": 384, "r": 16}), ("square", {"s": 160, "r": 64})):
+        ss = [_stream(name, kw, b, 4) for b in range(3)]
+        dims, ranks = ss[0][0], ss[0][1]
+        batch = _run_batch(torch, dims, ranks, [(s[2], s[3], s[4]) for s in ss])
+        monkeypatch.setenv("TTALS_SOLVE_KERNEL", "mma")
+        for b, s in enumerate(ss):
+            xa, sa = _run_alone(torch, dims, ranks, s[2], s[3], s[4])
+            for t in range(4):
+                rel = np.linalg.norm(batch[b][0][t] - xa[t]) / np.linalg.norm(xa[t])
+                assert rel <= 1e-3, (name, b, t, rel)
+        monkeypatch.setenv("TTALS_SOLVE_KERNEL", "tc")
+
+
+def test_batch_16_video_streams_full_size():
+    """16 full-size video streams: the batch takes the tcgen05 solve on its own (its row tiles
+    cover the SMs).  Streams share two frame sequences but start from different cores."""
+    torch = _torch()
+    T = 3
+    seqs = [_stream("video", {}, b, T) for b in range(2)]
+    dims, ranks = seqs[0][0], seqs[0][1]
+    streams = []
+    for b in range(16):
+        sq = seqs[b % 2]
+        c, g = synth.init_cores(dims, O.clamp_ranks(dims, ranks), seed=900 + b)
+        streams.append((sq[2], c, g))
+    batch = _run_batch(torch, dims, ranks, streams)
+    for b in (0, 1, 7, 15):
+        xa, sa = _run_alone(torch, dims, ranks, *streams[b])
+        for t in range(T):
+            rel = np.linalg.norm(batch[b][0][t] - xa[t]) / np.linalg.norm(xa[t])
+            assert rel <= 1e-3, (b, t, rel)
