@@ -66,7 +66,8 @@ typedef struct {
                             re-orthogonalisation (0 = default = 2)                        */
     int env_kernel;      /* fused path, environment kernel (S6): 0 = chosen by shape, 1 = the
                             clustered one, 2 = one CTA per column tile over all rows (ignored
-                            when its tile does not fit), 3 = streamed row stages           */
+                            when its tile does not fit), 3 = streamed row stages, 4 = streamed
+                            row stages on tcgen05 (ranks padded to 16, 32 or 64; else 3)  */
     int k1_split;        /* fused path, k-splits of the local solve (S4): 0 = chosen by
                             shape and batch size, else 1, 2, 4 or 8                         */
     int reserved[2];     /* must be zero                                                  */

@@ -132,6 +132,24 @@ bool encode_map_3d(CUtensorMap* map, const void* base, bool bf16, long long npla
   return r == CUDA_SUCCESS;
 }
 
+// 3-D map of the rounded basis Q1 (nplanes x rows x np, 16-bit), box np x 64 rows x 1 plane,
+// swizzled to the width of a row (np 16, 32, 64: 32-, 64-, 128-byte swizzle): the MN-major
+// operand layout of the tensor-core environment kernel
+bool encode_map_3d_q(CUtensorMap* map, const void* base, bool bf16, long long nplanes, long long rows, int np) {
+  PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+  if (!enc) return false;
+  cuuint64_t dim[3] = {(cuuint64_t)np, (cuuint64_t)rows, (cuuint64_t)nplanes};
+  cuuint64_t stride[2] = {(cuuint64_t)np * 2, (cuuint64_t)(rows * np) * 2};
+  cuuint32_t box[3] = {(cuuint32_t)np, 64u, 1u};
+  cuuint32_t estr[3] = {1u, 1u, 1u};
+  const CUtensorMapSwizzle sw = np == 16 ? CU_TENSOR_MAP_SWIZZLE_32B
+                                         : (np == 32 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_128B);
+  CUresult r = enc(map, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 3,
+                   const_cast<void*>(base), dim, stride, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, sw,
+                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
 size_t dtype_size(ttals_dtype d) {
   switch (d) {
     case TTALS_F64: return 8;
@@ -303,13 +321,14 @@ struct Impl final : ttals_stream {
   float2* fCC = nullptr;       // float-float partials of ||x^||^2 (env CTAs)
   // environment kernel: clustered row chunks, one CTA per 64-column tile over all rows, or
   // 64-column tiles with the rows streamed through a pipeline
-  enum { K2_CLUSTER = 0, K2_SINGLE = 1, K2_STREAM = 2 };
+  enum { K2_CLUSTER = 0, K2_SINGLE = 1, K2_STREAM = 2, K2_STREAM_TC = 3 };
   int k2_kind = K2_CLUSTER;
   // local solve kernel: mma.sync with k-splits in clusters, or tcgen05 over whole rows
   // (0: chosen per launch, 1: always tcgen05, -1: never)
   int k1_tc = 0;
   unsigned* fCounter = nullptr; // [nbatch][2]
   CUtensorMap mapB[2];          // TMA maps of fChb[p] (nbatch x r x rest_1, box 64 x NP)
+  CUtensorMap mapQ;             // TMA map of fQh (nbatch x I_1 x NP, box NP x 64), NP != 48
 
   int rows(int k) const { return (int)(full[k - 1] * dims[k - 1]); }  // r_{k-1} I_k
   int rk(int k) const { return (int)full[k]; }
@@ -395,6 +414,7 @@ struct Impl final : ttals_stream {
       TT_TRY(raise_smem_limit(fast::k_fast_solve_tc<TX, NP>));
       TT_TRY(raise_smem_limit(fast::k_fast_env1<TX, NP>));
       TT_TRY(raise_smem_limit(fast::k_fast_env_stream<TX, NP>));
+      if constexpr (NP != 48) TT_TRY(raise_smem_limit(fast::k_fast_env_tc<TX, NP>));
       TT_TRY(raise_smem_limit(fast::k_fast_env<TX, NP>));
       TT_TRY(raise_smem_limit(fast::k_fast_factor<TX, NP>));
     }
@@ -453,6 +473,7 @@ struct Impl final : ttals_stream {
         const std::string v(e);
         if (v == "cluster") k2_kind = K2_CLUSTER;
         else if (v == "stream") k2_kind = K2_STREAM;
+        else if (v == "streamtc") k2_kind = K2_STREAM_TC;
         else if (v == "single" && fits) k2_kind = K2_SINGLE;
       }
       // TTALS_SOLVE_KERNEL=tc|mma fixes the local-solve kernel (else chosen per launch)
@@ -460,11 +481,23 @@ struct Impl final : ttals_stream {
       if (cfg_env_kernel == 1) k2_kind = K2_CLUSTER;          // the stream's config wins
       else if (cfg_env_kernel == 2 && fits) k2_kind = K2_SINGLE;
       else if (cfg_env_kernel == 3) k2_kind = K2_STREAM;
+      else if (cfg_env_kernel == 4) k2_kind = K2_STREAM_TC;
       if (k2_kind == K2_SINGLE) {
         k2_nq = 1;
         k2_cols = (int)cdiv(J, fast::K2S_BN);
         k2_rch = fast::k2s_box_rows((int)M);      // TMA box height of the env kernel's X map
         k2_smem = b1;
+      }
+      if (k2_kind == K2_STREAM_TC && np_ == 48) k2_kind = K2_STREAM;   // no swizzle atom for 48
+      if (k2_kind == K2_STREAM_TC) {
+        k2_nq = 1;
+        k2_cols = (int)cdiv(J, fast::K2T_BN);
+        k2_rch = fast::K1_BM;
+        switch (np_) {
+          case 16: k2_smem = fast::k2t_smem_bytes<16>(); break;
+          case 32: k2_smem = fast::k2t_smem_bytes<32>(); break;
+          default: k2_smem = fast::k2t_smem_bytes<64>(); break;
+        }
       } else if (k2_kind == K2_STREAM) {
         k2_nq = 1;
         k2_cols = (int)cdiv(J, fast::K2P_BN);
@@ -514,6 +547,7 @@ struct Impl final : ttals_stream {
     const bool bf = std::is_same<TX, __nv_bfloat16>::value;
     for (int p = 0; p < 2; ++p)
       if (!encode_map_3d(&mapB[p], fChb[p], bf, nbatch, r, J, np_)) return TTALS_OK;
+    if (np_ != 48 && !encode_map_3d_q(&mapQ, fQh, bf, nbatch, M, np_)) return TTALS_OK;
     TT_CUDA(cudaMemset(fShiftb, 0, S * 2 * sizeof(int)));
     fast = true;
     return select_slot(0);
@@ -698,6 +732,13 @@ struct Impl final : ttals_stream {
         c2.attrs = at + 1;       // no cluster
         c2.numAttrs = 1;
         TT_CUDA(cudaLaunchKernelEx(&c2, fast::k_fast_env1<TX, NP>, mapX2, a2));
+      } else if (k2_kind == K2_STREAM_TC) {
+        if constexpr (NP != 48) {
+          c2.blockDim = dim3(fast::K2T_THREADS, 1, 1);
+          c2.attrs = at + 1;     // no cluster
+          c2.numAttrs = 1;
+          TT_CUDA(cudaLaunchKernelEx(&c2, fast::k_fast_env_tc<TX, NP>, mapX1, mapQ, a2));
+        }
       } else if (k2_kind == K2_STREAM) {
         c2.blockDim = dim3(fast::K2P_THREADS, 1, 1);
         c2.attrs = at + 1;       // no cluster
@@ -1198,7 +1239,7 @@ static ttals_status create_streams(int nbatch, int n_slice_modes, const int64_t*
     c = *cfg;
     for (int i = 0; i < 2; ++i)
       if (c.reserved[i] != 0) return TTALS_EINVAL;
-    if (c.env_kernel < 0 || c.env_kernel > 3) return TTALS_EINVAL;
+    if (c.env_kernel < 0 || c.env_kernel > 4) return TTALS_EINVAL;
     if (c.k1_split != 0 && c.k1_split != 1 && c.k1_split != 2 && c.k1_split != 4 && c.k1_split != 8)
       return TTALS_EINVAL;
     if (c.seed == 0) c.seed = 0x5eedull;

@@ -2030,6 +2030,258 @@ __global__ void __launch_bounds__(K2P_THREADS, 2)
   TTRACE(28);
 }
 
+// ================================================================ K2 on tcgen05 (batches)
+// F^T = X_(1)^T Q1 for a 128-column tile of X on the 5th-gen tensor cores: the I_1 rows stream
+// through 64-row stages (two 64 x 64 X boxes and the stage's Q1 rows, both by TMA), warp 0
+// issues the copies, warp 1's elected lane issues tcgen05.mma (M = 128 columns j, N = NP,
+// K = 16 rows per instruction; A = X^T and B = Q1 both MN-major in the TMA's swizzled
+// layouts; FP32 accumulator in TMEM) and frees each stage with tcgen05.commit.  Warps 2-5 read
+// the accumulator (TMEM lane = column j) into shared memory; then all 8 warps form the
+// statistics and write the state as in the other environment kernels.  Q1 of ranks padded
+// to 16, 32, 64 (swizzle 32, 64, 128 B).
+constexpr int K2T_BN = 128;
+constexpr int K2T_THREADS = 256;
+constexpr int K2T_MAXST = 4;
+template <int NP>
+__host__ __device__ constexpr int k2t_stages() { return NP <= 32 ? 4 : 3; }
+template <int NP>
+__host__ __device__ constexpr size_t k2t_smem_bytes() {
+  // X stages (64 x 256 B) | Q1 stages (64 x NP) | Nx, D2 (NP x NP each); F (128 x (r+1)
+  // floats) reuses the X stages after the loop
+  return 1024 + (size_t)k2t_stages<NP>() * (K2P_BM * 256 + K2P_BM * NP * 2) + (size_t)2 * NP * NP * 4;
+}
+// MN-major shared-memory descriptor: atoms of (row pitch) bytes x 8 rows along K, `lbo` bytes
+// between atoms along MN, `sbo` bytes between 8-row groups along K, swizzle code `layout`
+__device__ __forceinline__ uint64_t umma_desc_mn(uint32_t saddr, uint32_t lbo, uint32_t sbo, uint32_t layout) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+  d |= (uint64_t)1u << 46;
+  d |= (uint64_t)layout << 61;
+  return d;
+}
+template <int NP>
+__host__ __device__ constexpr uint32_t k2t_q_layout() { return NP == 16 ? 6u : (NP == 32 ? 4u : 2u); }
+
+template <typename TX, int NP>
+__global__ void __launch_bounds__(K2T_THREADS, 2)
+    k_fast_env_tc(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmQ, EnvArgs a0) {
+  const int zs = a0.zmap[blockIdx.z];     // grid plane z serves stream zs of the batch
+  const EnvArgs a = env_args_for_stream<TX, NP>(a0, zs, gridDim.x * gridDim.y);
+  static_assert(NP == 16 || NP == 32 || NP == 64, "Q1 swizzle atoms for ranks padded to 16, 32, 64");
+  constexpr int ST = k2t_stages<NP>();
+  static_assert(ST <= K2T_MAXST, "stages");
+  constexpr uint32_t XBOX = K2P_BM * 128, XB = 2 * XBOX, QB = K2P_BM * NP * 2;
+  constexpr uint32_t QPITCH = NP * 2;                 // bytes per Q1 row
+  constexpr uint32_t TCOLS = NP <= 32 ? 32 : 64;
+  // M = 128 columns, N = NP, A and B MN-major (transpose bits 15 and 16)
+  constexpr uint32_t IDESC = umma_idesc_f16<TX>(K2T_BN, NP) | (1u << 15) | (1u << 16);
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+  const int M = a.M, r = a.r, rr = r * r;
+  const uint32_t xs = smem_u32(smem);                          // X stage s at xs + s*XB
+  const uint32_t qs = xs + ST * XB;                            // Q1 stage s at qs + s*QB
+  float* sN = reinterpret_cast<float*>(smem + ST * (XB + QB)); // Nx, NP x NP, zero past r
+  float* sW = sN + NP * NP;                                    // D2 = W2 - I (NP x NP)
+  const int LDF = r + 1;
+  float* sF = reinterpret_cast<float*>(smem);                  // [128][r+1] after the loop
+  __shared__ __align__(8) uint64_t full[K2T_MAXST];
+  __shared__ __align__(8) uint64_t empty[K2T_MAXST];
+  __shared__ __align__(8) uint64_t done;
+  __shared__ uint32_t tmem_holder;
+  __shared__ float redf[64];
+  __shared__ int last_flag;
+  __shared__ int timeout_flag;
+
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int ct = blockIdx.x;
+  const long long j0 = (long long)ct * K2T_BN;
+  const int xcols = (a.J - j0 < K2T_BN) ? (int)(a.J - j0) : K2T_BN;
+  const int nt = (M + K2P_BM - 1) / K2P_BM;
+  const bool tr0 = (blockIdx.x == 0);
+  const bool W2_WRITER = (blockIdx.x == 0);
+  auto load_x = [&](int t, int st) {
+    const uint32_t bar = smem_u32(&full[st]);
+    mbar_arrive_expect_tx(bar, XB);
+    tma_load_3d(xs + st * XB, &tmX, (int)j0, t * K2P_BM, zs, bar);
+    tma_load_3d(xs + st * XB + XBOX, &tmX, (int)j0 + 64, t * K2P_BM, zs, bar);
+  };
+  auto load_q = [&](int t, int st) {
+    const uint32_t bar = smem_u32(&full[st]);
+    mbar_arrive_expect_tx(bar, QB);
+    tma_load_3d(qs + st * QB, &tmQ, 0, t * K2P_BM, zs, bar);
+  };
+
+  if (tid == 0) {
+    asm volatile("prefetch.tensormap [%0];\n" ::"l"(reinterpret_cast<uint64_t>(&tmX)) : "memory");
+    for (int st = 0; st < ST; ++st) {
+      mbar_init(smem_u32(&full[st]), 2);           // X arrival + Q1 arrival (expect_tx)
+      mbar_init(smem_u32(&empty[st]), 1);          // the MMA commit
+    }
+    mbar_init(smem_u32(&done), 1);
+    mbar_fence_init();
+    timeout_flag = 0;
+  }
+  if (warp == 1) tmem_alloc(smem_u32(&tmem_holder), TCOLS);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_holder;
+  if (warp == 0 && lane == 0)
+    for (int t = 0; t < ST && t < nt; ++t) load_x(t, t);
+  if (tr0) TTRACE(20);
+  pdl_wait();
+  pdl_trigger();
+  if (tr0) TTRACE(21);
+  const double xx = a.ctl->xx;
+  double sum_xx = 0.0, sum_ee = 0.0;
+  long long tcount = 0;
+  if (tid == 0) {
+    sum_xx = a.ctl->sum_xx;
+    sum_ee = a.ctl->sum_ee;
+    tcount = a.ctl->t;
+  }
+  if (a.ctl->skip) {
+    // non-finite slice: the new state is the old one
+    const long long nthr = (long long)gridDim.x * blockDim.x;
+    const long long me = (long long)blockIdx.x * blockDim.x + tid;
+    for (long long e = me; e < (long long)M * r; e += nthr) a.Qst[e] = a.Qold[e];
+    for (long long e = me; e < (long long)r * a.J; e += nthr) {
+      a.Cst[e] = a.Cold[e];
+      ((TX*)a.Chst)[e] = ((const TX*)a.Chold)[e];
+    }
+    for (long long e = me; e < rr; e += nthr) a.W2st[e] = a.W2old[e];
+    if (me == 0) *a.ch_shift = *a.ch_shift_old;
+    if (warp == 0 && lane == 0) {
+      // the X copies in flight land before the CTA exits (the Q1 arrival stands in)
+      bool ok = true;
+      for (int st = 0; st < ST && st < nt; ++st) {
+        mbar_arrive_expect_tx(smem_u32(&full[st]), 0);
+        ok = mbar_wait(smem_u32(&full[st]), 0) && ok;
+      }
+      if (!ok) a.ctl->latched = 5;
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 1) tmem_dealloc(tmem, TCOLS);
+    return;
+  }
+  if (warp == 0 && lane == 0)
+    for (int t = 0; t < ST && t < nt; ++t) load_q(t, t);
+  env_w2_nx<NP>(a.W2part, r, sW, sN, a.W2st, W2_WRITER);   // block-wide, while the copies fly
+  if (tr0) TTRACE(22);
+  if (warp == 0) {
+    if (lane == 0) {
+      int issued = nt < ST ? nt : ST;
+      for (int t = ST; t < nt; ++t) {
+        const int st = t % ST;
+        if (!mbar_wait(smem_u32(&empty[st]), (uint32_t)(((t / ST) - 1) & 1)) || timeout_flag) {
+          timeout_flag = 1;
+          break;
+        }
+        load_x(t, st);
+        load_q(t, st);
+        issued = t + 1;
+      }
+      if (timeout_flag) {
+        for (int t = issued - ST > 0 ? issued - ST : 0; t < issued; ++t)
+          mbar_wait(smem_u32(&full[t % ST]), (uint32_t)((t / ST) & 1));
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      for (int t = 0; t < nt; ++t) {
+        const int st = t % ST;
+        if (!mbar_wait(smem_u32(&full[st]), (uint32_t)((t / ST) & 1)) || timeout_flag) {
+          timeout_flag = 1;
+          break;
+        }
+        tc_fence_after();
+#pragma unroll
+        for (int kk = 0; kk < K2P_BM / 16; ++kk) {
+          // A = X^T: 64-column atoms (one per box, 8192 B apart), 8-row groups 1024 B apart
+          const uint64_t ad = umma_desc_mn(xs + st * XB + kk * 2048, XBOX, 1024, 2u);
+          // B = Q1: one atom of NP columns, 8-row groups 8 x QPITCH apart
+          const uint64_t bd = umma_desc_mn(qs + st * QB + kk * 16 * QPITCH, 8 * QPITCH, 8 * QPITCH, k2t_q_layout<NP>());
+          umma_f16(tmem, ad, bd, IDESC, (t | kk) != 0 ? 1u : 0u);
+        }
+        umma_commit(smem_u32(&empty[st]));
+      }
+      umma_commit(smem_u32(&done));
+    }
+    __syncwarp();
+  }
+  // the accumulator (lane = column j of the tile) -> sF[j][c]; the X stages are free now
+  if (warp >= 2 && warp < 6) {
+    const bool ok = mbar_wait(smem_u32(&done), 0);
+    if (!ok) timeout_flag = 1;
+    tc_fence_after();
+    const int q = warp & 3;
+    const int jl = q * 32 + lane;
+    float v[32];
+#pragma unroll
+    for (int c0 = 0; c0 < NP; c0 += 32) {
+      tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, v);
+#pragma unroll
+      for (int j = 0; j < 32; ++j)
+        if (c0 + j < r) sF[jl * LDF + c0 + j] = v[j];
+    }
+  }
+  tc_fence_before();
+  if (tid == 0 && timeout_flag) a.ctl->latched = 5;
+  __syncthreads();
+  if (tr0) TTRACE(23);
+  int shift = 0;
+  if (a.is_half && xx > 0.0) {
+    const float nrm = sqrtf((float)xx);
+    shift = nrm > 16384.f ? (int)ceilf(log2f(nrm / 16384.f)) : 0;
+  }
+  if (ct == 0 && tid == 0) *a.ch_shift = shift;
+  const float scale = ldexpf(1.0f, -shift);
+  float ph = 0.f, pl = 0.f;
+  env_columns_out<TX, NP>(sF, LDF, sN, xcols, r, a.J, j0, a.Cst, (TX*)a.Chst, scale, ph, pl);
+  const float2 cc_cta = ff_block_sum(ph, pl, redf);
+  if (tr0) TTRACE(24);
+  const int ncta = (int)gridDim.x;
+  if (tid == 0) {
+    a.cc_part[ct] = cc_cta;
+    __threadfence();
+    const unsigned dn = atomicAdd(a.counter, 1u);
+    last_flag = (dn == (unsigned)ncta - 1u);
+  }
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 1) tmem_dealloc(tmem, TCOLS);
+  if (!last_flag) return;
+  __threadfence();
+  float sh = 0.f, sl = 0.f;
+  for (int b0 = tid; b0 < ncta; b0 += 4 * K2T_THREADS) {
+    float2 vv[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+      vv[u] = (b0 + u * K2T_THREADS < ncta) ? __ldcg(a.cc_part + b0 + u * K2T_THREADS) : make_float2(0.f, 0.f);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) ff_add(sh, sl, vv[u].x, vv[u].y);
+  }
+  const float2 ccf = ff_block_sum(sh, sl, redf);
+  if (tid == 0) {
+    const double cc = (double)ccf.x + (double)ccf.y;
+    *a.counter = 0u;
+    Ctl* c = a.ctl;
+    if (!isfinite(cc)) c->latched = 4;
+    const double ccv = isfinite(cc) ? cc : 0.0;
+    const double ee = xx - ccv > 0.0 ? xx - ccv : 0.0;
+    c->cc = ccv;
+    c->ee = ee;
+    c->sum_xx = sum_xx + xx;
+    c->sum_ee = sum_ee + ee;
+    c->t = tcount + 1;
+  }
+  TTRACE(28);
+}
+
 // ================================================================ carry (masked steps)
 // Streams of a batch that take no step this time keep their state: copy it from the old
 // buffers into the new ones (the batch's buffer parity flips for every stream).  Grid plane

@@ -49,8 +49,8 @@ def test_invalid_arguments_rejected_before_cuda(lib):
     assert lib.ttals_create(2, dims, ranks, ctypes.byref(cfg), ctypes.byref(h)) == 1   # bad dtype
     cfg = T.Config(0, 1, 0, 0, 0, 0, (ctypes.c_int * 2)(1, 0))
     assert lib.ttals_create(2, dims, ranks, ctypes.byref(cfg), ctypes.byref(h)) == 1   # reserved != 0
-    cfg = T.Config(2, 1, 0, 0, 4, 0, (ctypes.c_int * 2)(0, 0))
-    assert lib.ttals_create(2, dims, ranks, ctypes.byref(cfg), ctypes.byref(h)) == 1   # env_kernel 4
+    cfg = T.Config(2, 1, 0, 0, 5, 0, (ctypes.c_int * 2)(0, 0))
+    assert lib.ttals_create(2, dims, ranks, ctypes.byref(cfg), ctypes.byref(h)) == 1   # env_kernel 5
     cfg = T.Config(2, 1, 0, 0, 0, 3, (ctypes.c_int * 2)(0, 0))
     assert lib.ttals_create(2, dims, ranks, ctypes.byref(cfg), ctypes.byref(h)) == 1   # k1_split 3
     ranks = (ctypes.c_int64 * 2)(65, 65)
