@@ -465,10 +465,11 @@ struct Impl final : ttals_stream {
         case 64: fits = fast::k2s_fits<64>((int)M, r); b1 = fast::k2s_smem_bytes<64>((int)M, r); break;
         default: break;
       }
-      // environment kernel: streamed row stages for batches (many column tiles, several CTAs
-      // per SM); for one stream the whole-column CTA when its tile fits, else the cluster
-      // kernel.  TTALS_ENV_KERNEL=cluster|single|stream overrides (single only if it fits).
-      k2_kind = nbatch > 1 ? K2_STREAM : (fits ? K2_SINGLE : K2_CLUSTER);
+      // environment kernel: for batches streamed row stages on tcgen05 (the mma.sync version
+      // for ranks padded to 48); for one stream the whole-column CTA when its tile fits, else
+      // the cluster kernel.  TTALS_ENV_KERNEL=cluster|single|stream|streamtc overrides (single
+      // only if it fits).
+      k2_kind = nbatch > 1 ? (np_ != 48 ? K2_STREAM_TC : K2_STREAM) : (fits ? K2_SINGLE : K2_CLUSTER);
       if (const char* e = std::getenv("TTALS_ENV_KERNEL")) {
         const std::string v(e);
         if (v == "cluster") k2_kind = K2_CLUSTER;

@@ -1,8 +1,8 @@
 """Autotuner of the fused path's schedule for a batch shape.
 
 A schedule is the environment kernel kind (``env_kernel``: 1 clustered, 2 one CTA per
-column tile over all rows, 3 streamed row stages, 4 streamed row stages on tcgen05) and the number of k-splits of the local
-solve (``k1_split``: 1, 2, 4, 8).  For a shape (slice dims, ranks, ingest, batch size) the
+column tile over all rows, 3 streamed row stages, 4 streamed row stages on tcgen05) and the
+number of k-splits of the local solve (``k1_split``: 1, 2, 4, 8).  For a shape (slice dims, ranks, ingest, batch size) the
 tuner times every environment kind at the default split, then every split with the best
 kind, each on seeded synthetic slices (device-timed with CUDA events over a few pushes,
 after warm-up), and keeps the fastest.  Results are cached per shape for the process.
