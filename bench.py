@@ -557,17 +557,31 @@ def table1_arm(orders=(5, 6, 7), I=30, rank=8, steps=6):
             "paper_note": "the paper's times are on its own hardware: context, not a target"}
 
 
-def e2e_arm(ingest, steps, pool_np, dist_on):
+def e2e_arm(ingest, steps, pool_np, dist_on, wire="ingest"):
     """Same metric through the C ABI from pinned HOST buffers: per step an H2D copy of the
     slice (copy stream, double-buffered device slot), the push, and an async D2H read of
-    the step's error statistics.  Copies overlap the previous step's update."""
+    the step's error statistics.  Copies overlap the previous step's update.
+    wire = "u8": the video frames are 8-bit pixels; the host holds them as bytes, the copy
+    moves bytes and ttals_widen_u8 widens them to the ingest type on the device (exact), on
+    the copy stream, before the push."""
     import torch
-    from paper_2606_31061_b300.ttals import Stream
+    from paper_2606_31061_b300.ttals import Stream, widen_u8
     st = Stream(DIMS, RANKS, ingest=ingest)
     P = min(16, pool_np.shape[0])
-    host = torch.from_numpy(pool_np[:P]).pin_memory()
+    if wire == "u8":
+        vals = torch.from_numpy(pool_np[:P])
+        if ingest == "f16":
+            vals = vals.view(torch.float16)
+        elif ingest == "bf16":
+            vals = vals.view(torch.bfloat16)
+        host = vals.float().round().clamp(0, 255).to(torch.uint8).pin_memory()
+        stage = [torch.empty(host.shape[1:], dtype=torch.uint8, device="cuda") for _ in range(2)]
+    else:
+        host = torch.from_numpy(pool_np[:P]).pin_memory()
+        stage = None
     slot_shape = host.shape[1:]
-    dev = [torch.empty(slot_shape, dtype=host.dtype, device="cuda") for _ in range(2)]
+    dev_dt = {"f16": torch.float16, "bf16": torch.bfloat16, "f32": torch.float32}[ingest]
+    dev = [torch.empty(slot_shape, dtype=dev_dt if wire == "u8" else host.dtype, device="cuda") for _ in range(2)]
     out = torch.zeros((steps, 4), dtype=torch.float64).pin_memory()
     comp = torch.cuda.current_stream()
     copy = torch.cuda.Stream()
@@ -580,7 +594,11 @@ def e2e_arm(ingest, steps, pool_np, dist_on):
         s = t % 2
         with torch.cuda.stream(copy):
             copy.wait_event(consumed[s])
-            dev[s].copy_(host[pingpong(t, P)], non_blocking=True)
+            if stage is None:
+                dev[s].copy_(host[pingpong(t, P)], non_blocking=True)
+            else:
+                stage[s].copy_(host[pingpong(t, P)], non_blocking=True)
+                widen_u8(stage[s], dev[s], stream=copy)
             copied[s].record(copy)
         comp.wait_event(copied[s])
         st.push_ptr(dev[s].data_ptr(), comp.cuda_stream)
@@ -735,7 +753,11 @@ def main():
     kname = {"solve": "level-1 local solve Y = X_(1) B^_1^T",
              "factor": "level-1 factorisation Q1 = orth(Y)",
              "env": "level-1 environment E_2 = G_1^T X_(1)"}[dom]
-    e2e = e2e_arm(args.ingest, args.e2e_steps, pool_np, dist_on)
+    # end to end: 8-bit video frames over the host link, widened on the device (the pixels
+    # are integers 0..255, exact in FP16); the FP16-frame variant is reported beside it
+    wire = "u8" if args.ingest in ("f16", "bf16") else "ingest"
+    e2e = e2e_arm(args.ingest, args.e2e_steps, pool_np, dist_on, wire=wire)
+    e2e16 = e2e_arm(args.ingest, args.e2e_steps, pool_np, dist_on) if wire == "u8" else None
     e2e_sec = e2e["seconds"]
     if dist_on:
         t = torch.tensor([e2e_sec], device="cuda")
@@ -817,7 +839,12 @@ def main():
                          "step_share": per[dom] / (r["ms_push"] / npush),
                          "ms_per_launch_all": per},
             "e2e": {"value": args.e2e_steps * world / e2e_sec, "unit": "slices/s",
-                    "h2d_bytes_per_step": e2e["h2d"], "d2h_bytes_per_step": e2e["d2h"]},
+                    "h2d_bytes_per_step": e2e["h2d"], "d2h_bytes_per_step": e2e["d2h"],
+                    "wire": "8-bit pixels, widened to the ingest type on the device (ttals_widen_u8)"
+                            if wire == "u8" else args.ingest},
+            "e2e_f16_wire": ({"value": args.e2e_steps / e2e16["seconds"], "unit": "slices/s",
+                              "h2d_bytes_per_step": e2e16["h2d"], "d2h_bytes_per_step": e2e16["d2h"]}
+                             if e2e16 else None),
             "gpu_launches": r["launches"],
             "clocks": r["clocks"],
             "batched": batched,
