@@ -416,7 +416,8 @@ struct Impl final : ttals_stream {
       TT_TRY(raise_smem_limit(fast::k_fast_env_stream<TX, NP>));
       if constexpr (NP != 48) TT_TRY(raise_smem_limit(fast::k_fast_env_tc<TX, NP>));
       TT_TRY(raise_smem_limit(fast::k_fast_env<TX, NP>));
-      TT_TRY(raise_smem_limit(fast::k_fast_factor<TX, NP>));
+      TT_TRY(raise_smem_limit(fast::k_fast_factor<TX, NP, 8>));
+      TT_TRY(raise_smem_limit(fast::k_fast_factor<TX, NP, 4>));
     }
     return TTALS_OK;
   }
@@ -686,18 +687,24 @@ struct Impl final : ttals_stream {
       ab.Qfb = fQfb;
       ab.ctl = ctl_base;
       std::memcpy(ab.zmap, zact, sizeof(zact));
+      // clusters of 8 one-CTA-per-SM CTAs fit the GPCs for up to 8 streams at once; beyond
+      // that clusters of 4 (twice the rows per CTA) keep the step in one wave
+      const int kbc = (n_act > 8 && fast::k1b_smem_bytes((int)dims[0], r, NP, 4) + 40 * 1024 <= 227 * 1024) ? 4 : 8;
       cudaLaunchAttribute atb[2];
       atb[0] = at[0];
-      atb[0].val.clusterDim.y = (unsigned)fast::KB_CLUSTER;
+      atb[0].val.clusterDim.y = (unsigned)kbc;
       atb[1] = at[1];
       cudaLaunchConfig_t cb{};
-      cb.gridDim = dim3(1, (unsigned)fast::KB_CLUSTER, (unsigned)n_act);
+      cb.gridDim = dim3(1, (unsigned)kbc, (unsigned)n_act);
       cb.blockDim = dim3(fast::K1B_THREADS, 1, 1);
-      cb.dynamicSmemBytes = fast::k1b_smem_bytes((int)dims[0], r, NP);
+      cb.dynamicSmemBytes = fast::k1b_smem_bytes((int)dims[0], r, NP, kbc);
       cb.stream = s;
       cb.attrs = atb;
       cb.numAttrs = 2;
-      TT_CUDA(cudaLaunchKernelEx(&cb, fast::k_fast_factor<TX, NP>, ab));
+      if (kbc == 4)
+        TT_CUDA(cudaLaunchKernelEx(&cb, fast::k_fast_factor<TX, NP, 4>, ab));
+      else
+        TT_CUDA(cudaLaunchKernelEx(&cb, fast::k_fast_factor<TX, NP, 8>, ab));
       ++nlaunch;
       TT_TRY(mark(3, s));
       // K2: environment
@@ -722,6 +729,7 @@ struct Impl final : ttals_stream {
       a2.W2old = fW2b[par];
       a2.ch_shift_old = fShiftb + par;
       a2.is_half = std::is_same<TX, __half>::value ? 1 : 0;
+      a2.w2_parts = kbc;
       std::memcpy(a2.zmap, zact, sizeof(zact));
       at[0].val.clusterDim.y = (unsigned)k2_nq;
       cudaLaunchConfig_t c2{};

@@ -785,7 +785,8 @@ __global__ void __launch_bounds__(K1T_THREADS, 1)
 }
 
 // ================================================================ K1b: r x r factor
-// A cluster of KB_CLUSTER CTAs; CTA q owns rows [q*nrows, (q+1)*nrows) of Y.
+// A cluster of KBC (8, or 4 for large batches) CTAs; CTA q owns rows [q*nrows, (q+1)*nrows)
+// of Y.
 //  1. Gram partial of my rows (FP32, 4 x 4 register blocks), W1 = the ranks' partials
 //     summed in rank order by every rank through distributed shared memory.
 //  2. Every rank factors the scaled Gram D W1 D = L L^T (FP32, one warp).
@@ -796,7 +797,7 @@ __global__ void __launch_bounds__(K1T_THREADS, 1)
 // A failed factorisation (scaled pivot <= 1e-4: rank-deficient or badly conditioned Y)
 // takes the FP64 Householder QR of Y on rank 0 instead.
 constexpr int K1B_THREADS = 256;
-constexpr int KB_CLUSTER = 8;
+constexpr int KB_CLUSTER = 8;       // the largest factor cluster: W2-partial slab stride
 
 struct FactorArgs {
   const float* Y;         // M x r
@@ -804,28 +805,29 @@ struct FactorArgs {
   int nxx, M, r;
   void* Qh;               // M x NP ingest-type Q1 (columns >= r zero)
   float* Qst;             // state: Q1 (M x r) as float
-  float* W2part;          // [KB_CLUSTER][NP*NP] W2 partials of the ranks' rows
+  float* W2part;          // [KB_CLUSTER][NP*NP] W2 partials of the ranks' rows (the first KBC)
   double* hh_work;        // 2*M*r doubles (fallback)
   float* Qfb;             // M x r (fallback Q, float)
   Ctl* ctl;
   unsigned char zmap[64];      // grid plane blockIdx.z -> stream (slot) of the batch
 };
 
-// rows of Y handled by one CTA of the factor cluster
-__host__ __device__ constexpr int k1b_rows(int M) { return ((M + KB_CLUSTER - 1) / KB_CLUSTER + 15) / 16 * 16; }
+// rows of Y handled by one CTA of a factor cluster of kbc CTAs
+__host__ __device__ constexpr int k1b_rows(int M, int kbc = KB_CLUSTER) { return ((M + kbc - 1) / kbc + 15) / 16 * 16; }
 // row groups of the Gram partial: 4 x 4 blocks of an NP x NP Gram per thread
 __host__ __device__ constexpr int k1b_rgroups(int np) {
   return K1B_THREADS / ((np / 4) * (np / 4)) > 0 ? K1B_THREADS / ((np / 4) * (np / 4)) : 1;
 }
 // dynamic shared memory: Y rows (fp32, stride NP+4) | Q1 rows (ingest type, stride NP+8) |
 // Gram partials of the row groups | this rank's Gram partial (W1, later W2)
-__host__ __device__ constexpr size_t k1b_smem_bytes(int M, int r, int np) {
-  return (size_t)k1b_rows(M) * (np + 4) * 4 + (size_t)(k1b_rows(M) + 16) * (np + 8) * 2 +
+__host__ __device__ constexpr size_t k1b_smem_bytes(int M, int r, int np, int kbc = KB_CLUSTER) {
+  return (size_t)k1b_rows(M, kbc) * (np + 4) * 4 + (size_t)(k1b_rows(M, kbc) + 16) * (np + 8) * 2 +
          (size_t)k1b_rgroups(np) * np * np * 4 + (size_t)np * np * 4 + 256 + 0 * r;
 }
 
-template <typename TX, int NP>
+template <typename TX, int NP, int KBC>
 __global__ void __launch_bounds__(K1B_THREADS, 1) k_fast_factor(FactorArgs a0) {
+  static_assert(KBC == 4 || KBC == 8, "factor cluster of 4 or 8 CTAs");
   // grid plane z serves stream zs of the batch: its state and scratch slabs
   const int zs = a0.zmap[blockIdx.z];
   FactorArgs a = a0;
@@ -849,7 +851,7 @@ __global__ void __launch_bounds__(K1B_THREADS, 1) k_fast_factor(FactorArgs a0) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int r = a.r, rr = r * r;
   const uint32_t crank = cluster_rank();
-  const int nrows = k1b_rows(a.M);
+  const int nrows = k1b_rows(a.M, KBC);
   const int row0 = (int)crank * nrows;
   const int myrows = (a.M - row0 < nrows) ? (a.M - row0 > 0 ? a.M - row0 : 0) : nrows;
   float* Ys = reinterpret_cast<float*>(smem);                               // [nrows][LDY]
@@ -932,15 +934,15 @@ __global__ void __launch_bounds__(K1B_THREADS, 1) k_fast_factor(FactorArgs a0) {
   {
     const uint32_t wb = smem_u32(Wp);
     for (int e0 = tid; e0 < rr; e0 += 4 * K1B_THREADS) {
-      float v[4][KB_CLUSTER];
+      float v[4][KBC];
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
         const int e = e0 + u * K1B_THREADS;
         const int ec = e < rr ? e : rr - 1;            // in-range address; value masked below
         const uint32_t la = wb + (uint32_t)((ec / r) * NP + ec % r) * 4u;
 #pragma unroll
-        for (int q = 0; q < KB_CLUSTER; ++q) {
-          const float x = dsmem_ld_rank(la, q, KB_CLUSTER);
+        for (int q = 0; q < KBC; ++q) {
+          const float x = dsmem_ld_rank(la, q, KBC);
           v[u][q] = e < rr ? x : 0.f;
         }
       }
@@ -948,7 +950,7 @@ __global__ void __launch_bounds__(K1B_THREADS, 1) k_fast_factor(FactorArgs a0) {
       for (int u = 0; u < 4; ++u) {
         float hi = 0.f, lo = 0.f;
 #pragma unroll
-        for (int q = 0; q < KB_CLUSTER; ++q) two_sum_acc(hi, lo, v[u][q]);
+        for (int q = 0; q < KBC; ++q) two_sum_acc(hi, lo, v[u][q]);
         if (e0 + u * K1B_THREADS < rr) W[e0 + u * K1B_THREADS] = hi + lo;
       }
     }
@@ -1183,7 +1185,7 @@ constexpr int K2_BN = 128;            // slice columns j per CTA of the clustere
 // 2 x 2 register-blocked product.  All K2_THREADS threads; ends synchronised.
 template <int NP>
 __device__ __forceinline__ void env_w2_nx(const float* __restrict__ W2part, int r, float* sD, float* sN,
-                                          float* W2st, bool write_state) {
+                                          float* W2st, bool write_state, int nparts) {
   const int tid = threadIdx.x;
   const bool worker = tid < K2_THREADS;       // extra (producer) warps only synchronise
   constexpr int PER = (NP * NP + K2_THREADS - 1) / K2_THREADS;
@@ -1195,7 +1197,7 @@ __device__ __forceinline__ void env_w2_nx(const float* __restrict__ W2part, int 
     const int e = tid + (u0 + u) * K2_THREADS;
     const int ec = e < NP * NP ? e : NP * NP - 1;
 #pragma unroll
-    for (int q = 0; q < KB_CLUSTER; ++q) v[u][q] = __ldcg(W2part + (size_t)q * NP * NP + ec);
+    for (int q = 0; q < KB_CLUSTER; ++q) v[u][q] = q < nparts ? __ldcg(W2part + (size_t)q * NP * NP + ec) : 0.f;
   }
 #pragma unroll
   for (int u = 0; u < G; ++u) {
@@ -1297,6 +1299,7 @@ struct EnvArgs {
   const float* W2old;
   const int* ch_shift_old;
   int is_half;          // 1: FP16 copy needs a range scale; 0: BF16
+  int w2_parts;         // W2 partials written by the factor kernel (its cluster size)
   unsigned char zmap[64];      // grid plane blockIdx.z -> stream (slot) of the batch
 };
 
@@ -1412,7 +1415,7 @@ __global__ void __launch_bounds__(K2_THREADS, 2)
       cp_async16(smem_u32(sQ + row * (NP + 8) + ch * 8), Qh + (ok ? (long long)gi * NP + ch * 8 : 0), ok ? 16u : 0u);
     }
     cp_async_commit();
-    env_w2_nx<NP>(a.W2part, r, sW, sN, a.W2st, W2_WRITER);
+    env_w2_nx<NP>(a.W2part, r, sW, sN, a.W2st, W2_WRITER, a.w2_parts);
     cp_async_wait<0>();
   }
   if (!mbar_wait(smem_u32(&xbar), 0)) timeout_flag = 1;
@@ -1657,7 +1660,7 @@ __global__ void __launch_bounds__(K2_THREADS, 1)
       cp_async16(qs + qswz<NP>(row, ch), Qh + (ok ? (long long)row * NP + ch * 8 : 0), ok ? 16u : 0u);
     }
     cp_async_commit();
-    env_w2_nx<NP>(a.W2part, r, sW, sN, a.W2st, W2_WRITER);
+    env_w2_nx<NP>(a.W2part, r, sW, sN, a.W2st, W2_WRITER, a.w2_parts);
     cp_async_wait<0>();
   }
   if (!mbar_wait(smem_u32(&xbar), 0)) timeout_flag = 1;
@@ -1902,7 +1905,7 @@ __global__ void __launch_bounds__(K2P_THREADS, 2)
   // producer refills stages as they are released and the consumers run the row loop
   if (producer)
     for (int t = 0; t < ST && t < nt; ++t) load_q(t, t);
-  env_w2_nx<NP>(a.W2part, r, sW, sN, a.W2st, W2_WRITER);
+  env_w2_nx<NP>(a.W2part, r, sW, sN, a.W2st, W2_WRITER, a.w2_parts);
   if (tr0) TTRACE(22);
   if (producer) {
     int issued = nt < ST ? nt : ST;
@@ -2170,7 +2173,7 @@ __global__ void __launch_bounds__(K2T_THREADS, 2)
   }
   if (warp == 0 && lane == 0)
     for (int t = 0; t < ST && t < nt; ++t) load_q(t, t);
-  env_w2_nx<NP>(a.W2part, r, sW, sN, a.W2st, W2_WRITER);   // block-wide, while the copies fly
+  env_w2_nx<NP>(a.W2part, r, sW, sN, a.W2st, W2_WRITER, a.w2_parts);   // block-wide, while the copies fly
   if (tr0) TTRACE(22);
   if (warp == 0) {
     if (lane == 0) {
