@@ -88,7 +88,9 @@ class _Pool:
         if init_cores is not None:
             cores, g = init_cores(sid, self.dims, self.batch.ranks)
         else:
-            cores, g = synth.init_cores(self.dims, self.batch.ranks, seed=hash(sid) & 0x7FFFFFFF)
+            # a stable seed (Python's hash of a string id changes from process to process)
+            import zlib
+            cores, g = synth.init_cores(self.dims, self.batch.ranks, seed=zlib.crc32(repr(sid).encode()) & 0x7FFFFFFF)
         self.batch.set_cores(cores, g, 0)
 
     def step(self, frames: Dict[int, object]):
