@@ -30,6 +30,21 @@ from .ttals import Stream
 _TORCH_DT = {"f16": "float16", "bf16": "bfloat16", "f32": "float32", "f64": "float64"}
 
 
+def plan_buckets(specs: Sequence[Tuple[Sequence[int], Sequence[int]]],
+                 max_batch: int = ttals.MAX_BATCH) -> List[Tuple[tuple, tuple, List[int]]]:
+    """Streams grouped into batches: one per distinct (dims, ranks) in order of first
+    appearance, each holding at most `max_batch` stream indices (in input order).  Returns
+    [(dims, ranks, members)]."""
+    keys: Dict[tuple, List[int]] = {}
+    for i, (d, r) in enumerate(specs):
+        keys.setdefault((tuple(int(v) for v in d), tuple(int(v) for v in r)), []).append(i)
+    out = []
+    for (d, r), members in keys.items():
+        for c0 in range(0, len(members), max_batch):
+            out.append((d, r, members[c0:c0 + max_batch]))
+    return out
+
+
 class _Bucket:
     def __init__(self, dims, ranks, ingest, members, depth, schedule):
         import torch
@@ -55,22 +70,17 @@ class Group:
         self.ingest = ingest
         self.depth = int(depth)
         self.specs = [(tuple(int(v) for v in d), tuple(int(v) for v in r)) for d, r in specs]
-        keys: Dict[tuple, List[int]] = {}
-        for i, (d, r) in enumerate(self.specs):
-            keys.setdefault((d, r), []).append(i)
         self.buckets: List[_Bucket] = []
         self.where: Dict[int, Tuple[int, int]] = {}
-        for (d, r), members in keys.items():
-            for c0 in range(0, len(members), ttals.MAX_BATCH):
-                part = members[c0:c0 + ttals.MAX_BATCH]
-                sched = None
-                if tune:
-                    from . import tune as _tune
-                    sched = _tune.best_schedule(d, r, len(part), ingest, steps=tune_steps)
-                b = _Bucket(d, r, ingest, part, self.depth, sched)
-                for slot, i in enumerate(part):
-                    self.where[i] = (len(self.buckets), slot)
-                self.buckets.append(b)
+        for d, r, part in plan_buckets(self.specs):
+            sched = None
+            if tune:
+                from . import tune as _tune
+                sched = _tune.best_schedule(d, r, len(part), ingest, steps=tune_steps)
+            b = _Bucket(d, r, ingest, part, self.depth, sched)
+            for slot, i in enumerate(part):
+                self.where[i] = (len(self.buckets), slot)
+            self.buckets.append(b)
         self._graph = None
         import torch
         self._side = [torch.cuda.Stream() for _ in self.buckets]
