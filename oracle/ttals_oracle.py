@@ -40,6 +40,11 @@ Two local-solve modes:
   least-squares solution when A_k^T A_k = I and B_k B_k^T = I);
 * ``lsq`` - the exact local least-squares solution for any B_k:
   G~_k = A_k^T X^ B_k^T (B_k B_k^T)^+  (Sec. 3.3, the Gram-matrix form).
+
+All slices seen so far (Eq. proposed-objective-slice, the per-slice form of Eq.
+proposed-objective-full): ``refit_temporal_rows`` gives the temporal rows that
+minimise it with the cores frozen at their time-t values, and ``global_objective``
+its value; both are pinned against dense least squares on tiny streams.
 """
 from __future__ import annotations
 
@@ -235,6 +240,38 @@ class OnlineTTALS:
                                                 - np.eye(full[k + 1]))) for k in range(m)))
             self.log = rec
         return xh
+
+
+def left_interface(cores) -> np.ndarray:
+    """A_n = G_1 x_2^1 G_2 x_3^1 ... x G_{n-1} as a (I_1...I_{n-1}) x r_{n-1} matrix
+    (the left interface of the temporal row, Sec. 3.2), contracted from the stored cores."""
+    a = np.ones((1, 1))
+    for c in cores:
+        r0, ik, r1 = c.shape
+        a = (a @ c.reshape(r0, ik * r1)).reshape(-1, r1)
+    return a
+
+
+def refit_temporal_rows(cores, slices) -> np.ndarray:
+    """Temporal rows g_n[1..t] that minimise Eq. proposed-objective-slice over all slices
+    seen so far with G_1..G_{n-1} held at their time-t values.  Each row is its own least
+    squares problem min ||x_i - A_n g||; with left-orthogonal cores (A_n^T A_n = I, Sec. 3.3)
+    its solution is A_n^T vec(x_i).  Returns an r_{n-1} x t matrix (column i = g_n[i])."""
+    a = left_interface(cores)
+    xs = np.stack([np.asarray(x, np.float64).reshape(-1) for x in slices], axis=1)
+    return a.T @ xs
+
+
+def global_objective(cores, rows, slices) -> float:
+    """Value of Eq. proposed-objective-slice (the all-slices form of Eq.
+    proposed-objective-full): sum_i ||x_i - G_1 x ... x G_{n-1} x g_n[i]||_F^2 for the
+    given cores and temporal rows (column i of ``rows`` = g_n[i])."""
+    a = left_interface(cores)
+    tot = 0.0
+    for i, x in enumerate(slices):
+        res = np.asarray(x, np.float64).reshape(-1) - a @ rows[:, i]
+        tot += float(res @ res)
+    return tot
 
 
 def run_stream(dims, ranks, cores, g, slices, mode="literal"):

@@ -33,6 +33,14 @@ MUTATIONS = {
     # local solve contracted with B_k instead of B_k^T on the wrong axis order
     "local_solve_transpose": ("gt = np.tensordot(t_k, B[k].T, axes=([2], [0]))",
                               "gt = np.tensordot(t_k[:, ::-1, :], B[k].T, axes=([2], [0]))"),
+    # global objective (all slices seen so far) summed over the current slice only; only the
+    # all-slices pin exercises it
+    "global_objective_current_only": ("    for i, x in enumerate(slices):",
+                                      "    for i, x in enumerate(slices[-1:]):"),
+    # stored cores contracted with the slice index and the right rank swapped (wrong index
+    # order of the materialised left interface); only the all-slices pin exercises it
+    "left_interface_index_order": ("a = (a @ c.reshape(r0, ik * r1)).reshape(-1, r1)",
+                                   "a = (a @ c.transpose(0, 2, 1).reshape(r0, ik * r1)).reshape(-1, r1)"),
 }
 
 PINS = [
@@ -44,6 +52,7 @@ PINS = [
     "test_monotonicity_prop41",
     "test_local_solve_is_bruteforce_least_squares",
     "test_temporal_row_is_bruteforce_lstsq",
+    "test_all_slices_batch_least_squares",
 ]
 
 

@@ -309,3 +309,56 @@ def test_stream_relative_error_definition():
     xs = [np.ones((2, 2)), 2 * np.ones((2, 2))]
     xh = [np.zeros((2, 2)), 2 * np.ones((2, 2))]
     assert abs(O.stream_relative_error(xs, xh) - math.sqrt(4 / 20)) < 1e-15
+
+
+def _dense_left_interface(cores):
+    """A_n by brute force: column b of A_n is the full contraction G_1 x ... x G_{n-1} x e_b,
+    formed element by element over every multi-index of the slice (tiny shapes only)."""
+    import itertools
+    dims = [c.shape[1] for c in cores]
+    rn = cores[-1].shape[2]
+    a = np.zeros((int(np.prod(dims)), rn))
+    for row, idx in enumerate(itertools.product(*[range(d) for d in dims])):
+        v = np.ones(1)
+        for c, i in zip(cores, idx):
+            v = v @ c[:, i, :]
+        a[row] = v
+    return a
+
+
+@pytest.mark.parametrize("mode", ["literal", "lsq"])
+def test_all_slices_batch_least_squares(mode):
+    """All slices seen so far (Eq. proposed-objective-slice): with the cores frozen after
+    step t, the temporal rows that minimise the objective over x_1..x_t, found by dense
+    LAPACK lstsq against a brute-force A_n, equal the oracle's refit A_n^T [x_1 .. x_t]
+    (<= 1e-12), its last column is the online g_n[t], and the oracle's global objective equals
+    the brute-force residual and lies above the Eckart-Young bound of the stacked slices at
+    rank r_{n-1}.  The global objective is reported beside the online RE (context: the
+    online RE uses time-varying cores, so no inequality links the two)."""
+    dims = (4, 3, 5)
+    sp = synth.make_stream("sensor", dims=dims, ranks=(3, 4, 2), noise=0.05, change_every=0)
+    xs = sp.take(6)
+    r = O.clamp_ranks(dims, sp.ranks)
+    cores, g = synth.init_cores(dims, r, seed=31)
+    st = O.OnlineTTALS(dims, r, cores, g, mode=mode)
+    seen, online = [], []
+    for x in xs:
+        online.append(st.step(x))
+        seen.append(x)
+        a_n = _dense_left_interface(st.G)
+        assert np.abs(a_n - O.left_interface(st.G)).max() <= 1e-13
+        stacked = np.stack([s.reshape(-1) for s in seen], axis=1)
+        ref, *_ = np.linalg.lstsq(a_n, stacked, rcond=None)
+        rows = O.refit_temporal_rows(st.G, seen)
+        assert rows.shape == (r[-1], len(seen))
+        assert np.abs(rows - ref).max() <= 1e-12 * max(1.0, np.abs(ref).max())
+        assert np.abs(rows[:, -1] - st.g).max() <= 1e-12 * max(1.0, np.abs(st.g).max())
+        brute = float(np.sum((stacked - a_n @ ref) ** 2))
+        obj = O.global_objective(st.G, rows, seen)
+        assert abs(obj - brute) <= 1e-12 * max(1.0, brute)
+        sv = np.linalg.svd(stacked, compute_uv=False)
+        assert obj >= float(np.sum(sv[r[-1]:] ** 2)) * (1 - 1e-12)
+    global_re = math.sqrt(obj / sum(float(np.sum(s ** 2)) for s in seen))
+    online_re = O.stream_relative_error(seen, online)
+    print(f"{mode}: global RE with frozen time-{len(seen)} cores {global_re:.4f}, online RE {online_re:.4f}")
+    assert 0.0 < global_re < 1.0 and 0.0 < online_re < 1.0
