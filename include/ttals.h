@@ -109,6 +109,17 @@ ttals_status ttals_set_cores(ttals_stream *s, const double *const *cores, const 
                              int64_t t);
 
 /*
+ * ttals_seed_cores - replace the state by the library's default random initial cores drawn
+ *   from `seed` ("Initialize orthogonal cores randomly", Algorithm 1): the generator and
+ *   order of ttals_create, so ttals_seed_cores(s, x) gives the cores that ttals_create with
+ *   cfg->seed = x gives its (first) stream; seed 0 means the default seed.  t becomes 0 and
+ *   latched errors are cleared.  On a batch it applies to the stream chosen by
+ *   ttals_batch_select (a serving loop seeds each stream it admits into a slot).
+ *   Synchronous.  Errors: EINVAL (NULL), ECUDA.
+ */
+ttals_status ttals_seed_cores(ttals_stream *s, uint64_t seed);
+
+/*
  * ttals_push_slice - one step of Algorithm 1 (Sec. 3.4) for the slice X_t.
  *   slice_dev: device pointer to prod(I_k) elements of `dtype` (C-order), 16-byte aligned.
  *   dtype must equal the stream's ingest dtype.
@@ -172,13 +183,22 @@ size_t ttals_device_bytes(const ttals_stream *s);
  *   whole update; *n_out = number of pushes.  Resets the totals.
  */
 uint64_t ttals_launch_count(const ttals_stream *s);
+/*
+ * ttals_debug_stall_solve - fault injection for tests (off unless called).  The next
+ *   n_pushes pushes of a stream on the fused FP16/BF16 path launch the level-1 local solve
+ *   (the k-split kernel) so that it issues no copy: its bounded wait for the first stage
+ *   gives up after about 100 ms, the kernel returns, the step is not committed and
+ *   TTALS_ETIMEOUT is latched for the next synchronising call.  Nothing faults and the
+ *   context stays usable.  n_pushes = 0 switches it off.  Errors: EINVAL.
+ */
+ttals_status ttals_debug_stall_solve(ttals_stream *s, int n_pushes);
 ttals_status ttals_stats_async(ttals_stream *s, double *out4, void *cuda_stream);
 ttals_status ttals_profile(ttals_stream *s, int enable);
 ttals_status ttals_profile_read(ttals_stream *s, double ms_out[4], int64_t *n_out);
 
 /*
  * ttals_slice_error_noalloc - allocation-free slice error (the paper has no
- *   counterpart: an evaluation helper around the per-slice error of Sec. 5.1).
+ *   counterpart; an evaluation helper of this library).
  *   Enqueues on cuda_stream the computation of out2_dev[0] = ||x||^2 and
  *   out2_dev[1] = ||x - y||^2 (FP64 sums in a fixed order, deterministic) for two
  *   device arrays of n elements, e.g. a slice x_t and the reconstruction written by

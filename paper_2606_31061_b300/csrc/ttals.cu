@@ -187,6 +187,7 @@ struct ttals_stream {
   size_t bytes = 0;
   std::vector<void*> allocs;
   unsigned long long nlaunch = 0;      // kernels launched by this stream (host counter)
+  int stall_pushes = 0;                // fault injection: pushes whose local solve issues no copy
   // optional timing of the level-1 kernels: CUDA events recorded on the launch stream
   bool profiling = false;
   // TTALS_NO_PDL=1 in the environment at creation: launch the fused kernels without
@@ -659,7 +660,9 @@ struct Impl final : ttals_stream {
       // quarters of the SMs (one CTA per SM); below that the k-split mma.sync kernel fills
       // the GPU better
       const int rows_tc = (int)cdiv(dims[0], fast::K1T_BM);
-      const bool use_tc = k1_tc > 0 || (k1_tc == 0 && 4LL * rows_tc * n_act >= 3LL * kSMs);
+      a1.stall = stall_pushes > 0 ? 1 : 0;
+      if (stall_pushes > 0) --stall_pushes;
+      const bool use_tc = !a1.stall && (k1_tc > 0 || (k1_tc == 0 && 4LL * rows_tc * n_act >= 3LL * kSMs));
       if (use_tc) {
         c1.gridDim = dim3((unsigned)rows_tc, 1, (unsigned)n_act);
         c1.blockDim = dim3(fast::K1T_THREADS, 1, 1);
@@ -1234,6 +1237,23 @@ const char* ttals_status_string(ttals_status st) {
 
 const char* ttals_last_error(void) { return g_last_err.c_str(); }
 
+// the selected stream's state <- the next draw of the default initial cores ("Initialize
+// orthogonal cores randomly", Algorithm 1): Gaussian entries in core order, then g_n; the
+// push re-orthogonalises them (Sec. 3.4.1), so they need not be orthogonal here
+static ttals_status set_default_cores(ttals_stream* s, SplitMix64& rng) {
+  const int m = s->m;
+  std::vector<std::vector<double>> cores(m);
+  std::vector<const double*> ptrs(m);
+  std::vector<double> g((size_t)s->full[m]);
+  for (int k = 1; k <= m; ++k) {
+    cores[k - 1].resize((size_t)s->core_elems(k));
+    for (double& v : cores[k - 1]) v = rng.gauss();
+    ptrs[k - 1] = cores[k - 1].data();
+  }
+  for (double& v : g) v = rng.gauss();
+  return s->set_cores(ptrs.data(), g.data(), 0);
+}
+
 // one stream (nbatch = 1) or a batch of nbatch streams of one shape that share launches
 static ttals_status create_streams(int nbatch, int n_slice_modes, const int64_t* dims, const int64_t* ranks,
                                    const ttals_config* cfg, ttals_stream** out) {
@@ -1321,18 +1341,9 @@ static ttals_status create_streams(int nbatch, int n_slice_modes, const int64_t*
   }
   // default initial cores: Gaussian (SplitMix64 + Box-Muller), one draw per stream of a batch
   SplitMix64 rng{c.seed};
-  std::vector<std::vector<double>> cores(m);
-  std::vector<const double*> ptrs(m);
-  std::vector<double> g((size_t)s->full[m]);
   for (int b = 0; b < nbatch && st == TTALS_OK; ++b) {
-    for (int k = 1; k <= m; ++k) {
-      cores[k - 1].resize((size_t)s->core_elems(k));
-      for (double& v : cores[k - 1]) v = rng.gauss();
-      ptrs[k - 1] = cores[k - 1].data();
-    }
-    for (double& v : g) v = rng.gauss();
     st = s->select_slot(b);
-    if (st == TTALS_OK) st = s->set_cores(ptrs.data(), g.data(), 0);
+    if (st == TTALS_OK) st = set_default_cores(s, rng);
   }
   if (st == TTALS_OK) st = s->select_slot(0);
   if (st != TTALS_OK) {
@@ -1411,6 +1422,12 @@ ttals_status ttals_set_cores(ttals_stream* s, const double* const* cores, const 
   return s->set_cores(cores, g, t);
 }
 
+ttals_status ttals_seed_cores(ttals_stream* s, uint64_t seed) {
+  if (!s) return TTALS_EINVAL;
+  SplitMix64 rng{seed ? seed : 0x5eedull};
+  return set_default_cores(s, rng);
+}
+
 ttals_status ttals_push_slice(ttals_stream* s, const void* slice_dev, ttals_dtype dtype, void* cuda_stream) {
   if (!s || !slice_dev) return TTALS_EINVAL;
   if (s->nbatch != 1) return TTALS_ESTATE;          // a batch steps through ttals_push_batch
@@ -1487,6 +1504,12 @@ int ttals_debug_trace_cta(unsigned long long* out, int n) {
 #endif
 
 uint64_t ttals_launch_count(const ttals_stream* s) { return s ? (uint64_t)s->nlaunch : 0; }
+
+ttals_status ttals_debug_stall_solve(ttals_stream* s, int n_pushes) {
+  if (!s || n_pushes < 0) return TTALS_EINVAL;
+  s->stall_pushes = n_pushes;
+  return TTALS_OK;
+}
 
 ttals_status ttals_stats_async(ttals_stream* s, double* out4, void* cuda_stream) {
   if (!s || !out4) return TTALS_EINVAL;

@@ -267,6 +267,8 @@ struct SolveArgs {
   float* Y;               // M x r
   float2* xx_part;        // [row tiles * splits] float-float partials of ||x||^2
   Ctl* ctl;
+  int stall;              // fault injection (k_fast_solve): issue no copy, so that the
+                          // consumers' first bounded wait runs out (0 in normal use)
   unsigned char zmap[64];      // grid plane blockIdx.z -> stream (slot) of the batch
 };
 
@@ -346,7 +348,7 @@ __global__ void __launch_bounds__(K1_THREADS, 2)
   if (tr0) TTRACE(0);
   TTRACE_CTA(0);
   // A tiles do not depend on the previous kernel: start them before the dependency wait
-  if (producer && lane == 0) {
+  if (producer && lane == 0 && !a.stall) {
     for (int t = 0; t < ST && t < ntk; ++t) {
       mbar_arrive_expect_tx(smem_u32(&full[t]), ABYTES);
       load_a(t, t);
@@ -371,7 +373,10 @@ __global__ void __launch_bounds__(K1_THREADS, 2)
   for (int j = 0; j < NT; ++j) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.f;
   float ssh = 0.f, ssl = 0.f;    // ||x||^2 of the tiles seen by this thread (float-float)
   if (producer) {
-    if (lane == 0) {
+    if (lane == 0 && a.stall) {
+      // fault injection: no copy is issued, nothing is in flight; the consumers' wait on
+      // stage 0 gives up after its bound and the step is marked failed
+    } else if (lane == 0) {
       int issued = ntk < ST ? ntk : ST;
       for (int t = 0; t < issued; ++t) {
         if (bzero) {
@@ -466,7 +471,9 @@ __global__ void __launch_bounds__(K1_THREADS, 2)
   }
   const float2 ss_cta = ff_block_sum(ssh, ssl, redf);
   if (tid == 0) {
-    a.xx_part[(size_t)rt * nsplit + crank] = ss_cta;    // one partial of ||x||^2 per CTA
+    // one partial of ||x||^2 per CTA; a CTA whose wait gave up writes NaN, which makes the
+    // factor kernel mark the step skipped (not committed) while ETIMEOUT stays latched
+    a.xx_part[(size_t)rt * nsplit + crank] = timeout_flag ? make_float2(__int_as_float(0x7fc00000), 0.f) : ss_cta;
     if (timeout_flag) a.ctl->latched = 5;
   }
   cluster_sync();
@@ -776,7 +783,8 @@ __global__ void __launch_bounds__(K1T_THREADS, 1)
   tc_fence_before();
   const float2 ss_cta = ff_block_sum(ssh, ssl, redf);   // (includes a block barrier)
   if (tid == 0) {
-    a.xx_part[rt] = ss_cta;                   // one partial of ||x||^2 per row tile
+    // one partial of ||x||^2 per row tile; NaN after a wait gave up (the step is not committed)
+    a.xx_part[rt] = timeout_flag ? make_float2(__int_as_float(0x7fc00000), 0.f) : ss_cta;
     if (timeout_flag) a.ctl->latched = 5;
   }
   __syncthreads();
@@ -894,7 +902,7 @@ __global__ void __launch_bounds__(K1B_THREADS, 1) k_fast_factor(FactorArgs a0) {
       const double xs = (double)xh + (double)xl;
       flags[0] = !isfinite(xs);
       flags[1] = 0;
-      if (crank == 0) a.ctl->xx = xs;
+      if (crank == 0 && !flags[0]) a.ctl->xx = xs;   // a skipped step keeps the committed value
     }
   }
   cp_async_wait<0>();
@@ -969,7 +977,7 @@ __global__ void __launch_bounds__(K1B_THREADS, 1) k_fast_factor(FactorArgs a0) {
   if (crank == 0 && tid == 0) {
     a.ctl->fallback[0] = 0;
     a.ctl->skip = flags[0];
-    if (flags[0]) a.ctl->latched = 4;
+    if (flags[0] && a.ctl->latched != 5) a.ctl->latched = 4;   // a solve timeout stays ETIMEOUT
   }
   if (flags[0]) {           // uniform across the cluster (identical W1 and ||x||^2)
     cluster_wait();

@@ -81,17 +81,17 @@ class _Pool:
             self.bytes += self.stage.numel()
 
     def reset_slot(self, slot, sid, init_cores=None):
-        """A new stream in this slot: its initial cores (seeded by the stream id unless
-        `init_cores` gives them), step count and statistics zero."""
-        from . import synth
+        """A new stream in this slot: its initial cores (the library's default random cores
+        seeded by the stream id, unless `init_cores` gives them), step count and statistics
+        zero."""
         self.batch.select(slot)
         if init_cores is not None:
             cores, g = init_cores(sid, self.dims, self.batch.ranks)
+            self.batch.set_cores(cores, g, 0)
         else:
             # a stable seed (Python's hash of a string id changes from process to process)
             import zlib
-            cores, g = synth.init_cores(self.dims, self.batch.ranks, seed=zlib.crc32(repr(sid).encode()) & 0x7FFFFFFF)
-        self.batch.set_cores(cores, g, 0)
+            self.batch.seed_cores((zlib.crc32(repr(sid).encode()) & 0x7FFFFFFF) + 1)
 
     def step(self, frames: Dict[int, object]):
         """frames: slot -> pinned host tensor.  Returns the step's completion event."""

@@ -26,7 +26,8 @@ EXPORTS = ("ttals_create", "ttals_destroy", "ttals_effective_ranks", "ttals_set_
            "ttals_sync", "ttals_device_bytes", "ttals_status_string", "ttals_last_error",
            "ttals_launch_count", "ttals_stats_async", "ttals_profile", "ttals_profile_read",
            "ttals_slice_error_noalloc", "ttals_create_batch", "ttals_push_batch", "ttals_batch_select",
-           "ttals_batch_size", "ttals_push_batch_masked", "ttals_widen_u8")
+           "ttals_batch_size", "ttals_push_batch_masked", "ttals_widen_u8", "ttals_seed_cores",
+           "ttals_debug_stall_solve")
 
 
 class TTALSError(RuntimeError):
@@ -79,6 +80,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "ttals_push_batch_masked": (ctypes.c_int, [VP, VP, ctypes.c_int, ctypes.c_uint64, VP]),
         "ttals_widen_u8": (ctypes.c_int, [VP, VP, ctypes.c_int, ctypes.c_int64, VP]),
         "ttals_batch_size": (ctypes.c_int, [VP]),
+        "ttals_seed_cores": (ctypes.c_int, [VP, ctypes.c_uint64]),
+        "ttals_debug_stall_solve": (ctypes.c_int, [VP, ctypes.c_int]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -166,6 +169,11 @@ class Stream:
         _check(load().ttals_set_cores(self._h, ptrs, gg.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
                                       int(t)), "ttals_set_cores")
 
+    def seed_cores(self, seed: int):
+        """ttals_seed_cores: the library's default random initial cores drawn from `seed`
+        (those ttals_create gives for cfg.seed = seed), t = 0."""
+        _check(load().ttals_seed_cores(self._h, ctypes.c_uint64(int(seed))), "ttals_seed_cores")
+
     def push(self, slice_tensor, stream=None):
         """Enqueue one update for a contiguous device tensor of the ingest dtype."""
         _check(load().ttals_push_slice(self._h, ctypes.c_void_p(slice_tensor.data_ptr()),
@@ -241,6 +249,11 @@ class Stream:
         """ttals_batch_select: later per-stream calls refer to stream `index` of the batch."""
         _check(load().ttals_batch_select(self._h, int(index)), "ttals_batch_select")
 
+    def debug_stall_solve(self, n_pushes: int):
+        """ttals_debug_stall_solve: the next n_pushes pushes time out in the local solve
+        (bounded wait; ETIMEOUT latched, the step not committed).  Test hook."""
+        _check(load().ttals_debug_stall_solve(self._h, int(n_pushes)), "ttals_debug_stall_solve")
+
     def profile(self, enable: bool):
         _check(load().ttals_profile(self._h, 1 if enable else 0), "ttals_profile")
 
@@ -264,12 +277,41 @@ def widen_u8(src, dst, stream=None):
 _TORCH_DTYPES = {"float64": "f64", "float32": "f32", "float16": "f16", "bfloat16": "bf16"}
 
 
+def check_noalloc_args(x, y, out2, device: int):
+    """Argument checks of slice_error_noalloc, on tensor metadata only (no device access).
+
+    The C entry point receives raw pointers and one element count and cannot see a short
+    or strided y, an out2 that is too small, or a tensor on another device; any of those
+    would make its kernel read or write out of bounds.  Raises TTALSError(EINVAL)."""
+    def bad(why):
+        raise TTALSError(1, "ttals_slice_error_noalloc", why)
+    for name, t in (("x", x), ("y", y), ("out2", out2)):
+        if not getattr(t, "is_cuda", False):
+            bad(f"{name} is not a CUDA tensor")
+        if t.device.index != device:
+            bad(f"{name} is on cuda:{t.device.index}, the current device is cuda:{device}")
+        if not t.is_contiguous():
+            bad(f"{name} is not contiguous")
+    if y.numel() != x.numel():
+        bad(f"y has {y.numel()} elements, x has {x.numel()}")
+    if str(x.dtype).replace("torch.", "") not in _TORCH_DTYPES:
+        bad(f"x dtype {x.dtype} is not float64/float32/float16/bfloat16")
+    if str(y.dtype).replace("torch.", "") not in ("float64", "float32"):
+        bad(f"y dtype {y.dtype} is not float64/float32")
+    if str(out2.dtype).replace("torch.", "") != "float64" or out2.numel() < 2:
+        bad("out2 must be a float64 tensor of at least 2 elements")
+
+
 def slice_error_noalloc(x, y, out2, stream=None):
     """ttals_slice_error_noalloc: enqueue out2[0] = ||x||^2, out2[1] = ||x - y||^2.
 
-    x, y: contiguous CUDA tensors of the same element count (y float64 or float32);
-    out2: a CUDA float64 tensor of 2 elements.  Allocates no device memory.
+    x, y: contiguous CUDA tensors of the same element count on the current device
+    (y float64 or float32); out2: a CUDA float64 tensor of at least 2 elements on the same
+    device.  Allocates no device memory.  Bad arguments raise TTALSError(EINVAL) before the
+    call (check_noalloc_args).
     """
+    import torch
+    check_noalloc_args(x, y, out2, torch.cuda.current_device())
     xt = DTYPES[_TORCH_DTYPES[str(x.dtype).replace("torch.", "")]]
     yt = DTYPES[_TORCH_DTYPES[str(y.dtype).replace("torch.", "")]]
     lib = load()

@@ -79,3 +79,43 @@ def test_no_device_fails_loudly(lib):
     ranks = (ctypes.c_int64 * 2)(2, 2)
     assert lib.ttals_create(2, dims, ranks, None, ctypes.byref(h)) == 3      # ECUDA, no fallback
     assert not h.value
+
+
+class _FakeTensor:
+    """Tensor metadata only (what the binding's argument checks read)."""
+
+    def __init__(self, n=16, dtype="torch.float32", cuda=True, dev=0, contiguous=True):
+        import types
+        self.is_cuda, self._n, self.dtype, self._c = cuda, n, dtype, contiguous
+        self.device = types.SimpleNamespace(index=dev if cuda else None)
+
+    def numel(self):
+        return self._n
+
+    def is_contiguous(self):
+        return self._c
+
+
+def test_noalloc_wrapper_rejects_bad_arguments_on_the_host():
+    """slice_error_noalloc validates what the C entry point cannot see (it gets one element
+    count and raw pointers): each bad case raises EINVAL before any library call."""
+    F = _FakeTensor
+    good = dict(x=F(16, "torch.float16"), y=F(16, "torch.float32"), out2=F(2, "torch.float64"))
+    T.check_noalloc_args(device=0, **good)          # control: accepted
+    bad_cases = [
+        dict(good, x=F(16, "torch.float16", cuda=False)),          # host tensor
+        dict(good, y=F(15, "torch.float32")),                      # shorter y
+        dict(good, y=F(17, "torch.float32")),                      # longer y
+        dict(good, x=F(16, "torch.float16", contiguous=False)),    # strided x
+        dict(good, y=F(16, "torch.float32", contiguous=False)),    # strided y
+        dict(good, y=F(16, "torch.float16")),                      # y not float64/float32
+        dict(good, x=F(16, "torch.int32")),                        # x not a float type
+        dict(good, out2=F(2, "torch.float32")),                    # out2 not float64
+        dict(good, out2=F(1, "torch.float64")),                    # out2 too small
+        dict(good, out2=F(2, "torch.float64", dev=1)),             # out2 on another device
+        dict(good, y=F(16, "torch.float32", dev=1)),               # y on another device
+    ]
+    for case in bad_cases:
+        with pytest.raises(T.TTALSError) as ei:
+            T.check_noalloc_args(device=0, **case)
+        assert ei.value.code == 1

@@ -151,3 +151,28 @@ def test_u8_wire_bitwise_equals_f16_wire():
         out.append(_served(torch, srv, 0, dims))
         srv.close()
     assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+
+
+def test_seed_cores_matches_create_seed():
+    """ttals_seed_cores draws the library's own default initial cores: a batch slot seeded with
+    x steps bitwise like a fresh stream created with cfg.seed = x (the serving loop seeds every
+    admitted stream this way, without the test-input generator)."""
+    torch = _torch()
+    from paper_2606_31061_b300.ttals import Stream
+    dims, ranks = (96, 128, 3), (32, 9, 3)
+    frames = [f.cuda() for f in _frames(torch, "video", {"dims": dims}, 3, 3)]
+    out_a = torch.empty(dims, dtype=torch.float64, device="cuda")
+    out_b = torch.empty_like(out_a)
+    a = Stream(dims, ranks, ingest="f16", seed=777)
+    b = Stream(dims, ranks, ingest="f16", seed=123)
+    for f in frames[:2]:
+        b.push(f)                                  # some history that the reseed must erase
+    b.seed_cores(777)
+    assert b.step() == 0
+    for f in frames:
+        a.push(f)
+        b.push(f)
+    a.reconstruct(out_a, "f64")
+    b.reconstruct(out_b, "f64")
+    assert torch.equal(out_a, out_b)
+    assert np.array_equal(a.stats(), b.stats()) and a.step() == b.step() == 3
