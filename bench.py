@@ -152,11 +152,11 @@ def traffic_record(kernel, sub=None):
     return None
 
 
-def time_arm(ingest, steps, warmup, pool, dist_on, sampler_idx):
+def time_arm(ingest, steps, warmup, pool, dist_on, sampler_idx, factor="fp64", dims=None, ranks=None):
     """Device-timed throughput of `steps` pushes; per-kernel event timing on the launch stream."""
     import torch
     from paper_2606_31061_b300.ttals import Stream
-    st = Stream(DIMS, RANKS, ingest=ingest)
+    st = Stream(dims or DIMS, ranks or RANKS, ingest=ingest, factor=factor)
     P = pool.shape[0]
     stream = torch.cuda.current_stream()
     h = stream.cuda_stream
@@ -621,6 +621,93 @@ def e2e_arm(ingest, steps, pool_np, dist_on, wire="ingest"):
     return dict(seconds=t1 - t0, h2d=slice_bytes, d2h=4 * 8)
 
 
+SENSOR_DIMS = (32, 32, 32, 32)
+SENSOR_RANKS = (16, 32, 32, 16)
+
+
+def sensor_arm(ingest, steps, warmup):
+    """Sensor-shaped 5th-order stream (32^4 slices, ranks (16,32,32,16), abrupt change every 200
+    steps), device-resident pool of frames larger than L2 played forward and backward."""
+    import torch
+    from paper_2606_31061_b300 import synth
+    sp = synth.make_stream("sensor")
+    es = 4 if ingest == "f32" else 2
+    nfr = int(math.ceil(200e6 / (int(np.prod(SENSOR_DIMS)) * es)))
+    pool_np = np.stack([synth.round_to_ingest(x, ingest)[0] for x in sp.frames(nfr)])
+    pool = to_device(pool_np, ingest)
+    r = time_arm(ingest, steps, warmup, pool, False, None, dims=SENSOR_DIMS, ranks=SENSOR_RANKS)
+    sb = int(np.prod(SENSOR_DIMS)) * es
+    out = {"value": steps / (r["ms"] / 1000.0), "unit": "slices/s", "ms_per_step": r["ms"] / steps,
+           "slice_gbs": steps / (r["ms"] / 1000.0) * sb / 1e9, "re": r["re"], "gpu_launches": r["launches"],
+           "pool_mb": pool.numel() * es / 1e6}
+    del pool
+    torch.cuda.empty_cache()
+    return out
+
+
+def oracle_check(name, dims, ranks, ingests, nframes, init_seed=7, **kw):
+    """The FP64 oracle and the GPU path on the same first `nframes` frames of a stream, from the
+    same initial cores, each ingest rounding the frames the way the GPU ingests them (ingests
+    whose rounded frames coincide, as FP16 and FP32 do for 8-bit pixels, share one oracle
+    run): per ingest the stream RE of both (Sec. 5.1), |RE_gpu - RE_oracle| and the largest
+    per-slice relative difference of the reconstructions.  Also the oracle's time per slice."""
+    import torch
+    from oracle import ttals_oracle as O
+    from paper_2606_31061_b300 import synth
+    from paper_2606_31061_b300.ttals import Stream
+    sp = synth.make_stream(name, **kw)
+    frames = sp.take(nframes)
+    r = O.clamp_ranks(dims, ranks)
+    cores, g = synth.init_cores(dims, r, seed=init_seed)
+    tdt = {"f64": torch.float64, "f32": torch.float32, "f16": torch.float16, "bf16": torch.bfloat16}
+    groups = []                       # [(ingests sharing the rounded values)]
+    for ing in ingests:
+        e0 = synth.round_to_ingest(frames[0], ing)[1]
+        for grp in groups:
+            if np.array_equal(synth.round_to_ingest(frames[0], grp[0])[1], e0):
+                grp.append(ing)
+                break
+        else:
+            groups.append([ing])
+    res, orc_s, orc_n = {}, 0.0, 0
+    for grp in groups:
+        sts = {}
+        for ing in grp:
+            sts[ing] = Stream(dims, ranks, ingest=ing)
+            sts[ing].set_cores(cores, g)
+        out = torch.empty(tuple(dims), dtype=torch.float64, device="cuda")
+        orc = O.OnlineTTALS(dims, r, cores, g)
+        acc = {ing: [0.0, 0.0] for ing in grp}      # [sum ||x - x^_gpu||^2, worst per-slice]
+        num_o = den = 0.0
+        for x in frames:
+            exact = None
+            for ing in grp:
+                payload, exact = synth.round_to_ingest(x, ing)
+                t = torch.from_numpy(np.ascontiguousarray(payload))
+                if ing in ("f16", "bf16"):
+                    t = t.view(tdt[ing])
+                sts[ing].push(t.cuda())
+            a = time.perf_counter()
+            xo = orc.step(exact)
+            orc_s += time.perf_counter() - a
+            orc_n += 1
+            nxo = max(float(np.linalg.norm(xo)), 1e-300)
+            for ing in grp:
+                sts[ing].reconstruct(out, "f64")
+                xg = out.cpu().numpy()
+                acc[ing][0] += float(np.sum((exact - xg) ** 2))
+                acc[ing][1] = max(acc[ing][1], float(np.linalg.norm(xg - xo)) / nxo)
+            num_o += float(np.sum((exact - xo) ** 2))
+            den += float(np.sum(exact * exact))
+        re_o = math.sqrt(num_o / den)
+        for ing in grp:
+            sts[ing].close()
+            re_g = math.sqrt(acc[ing][0] / den)
+            res[ing] = {"re_gpu": re_g, "re_oracle": re_o, "abs_diff_re": abs(re_g - re_o),
+                        "max_rel_diff_per_slice": acc[ing][1]}
+    return {"frames": nframes, "per_ingest": res, "oracle_s_per_slice": orc_s / max(1, orc_n)}
+
+
 def cpu_baseline_oracle(ingest, budget_s=15.0, max_steps=None):
     """The FP64 oracle (test infrastructure) on the host cores, on a bounded prefix of the
     same stream: returns (slices/s, steps, threads, seconds)."""
@@ -701,6 +788,9 @@ def main():
     ap.add_argument("--c4-steps", type=int, default=200, help="mixed-shape group steps (0: skip)")
     ap.add_argument("--serve-seconds", type=float, default=2.0, help="serving-loop traffic (0: skip)")
     ap.add_argument("--table1", type=int, default=1, help="high-order scalability arm (0: skip)")
+    ap.add_argument("--sensor-steps", type=int, default=300, help="sensor-shaped stream arm (0: skip)")
+    ap.add_argument("--oracle-frames", type=int, default=40,
+                    help="prefix on which the oracle is timed and compared with the GPU path")
     ap.add_argument("--profile-case", default=None, choices=["single", "batched"],
                     help="for profilers: run --warmup + --steps pushes of one video stream, or of a "
                          "batch of --batch video streams, untimed, and print no bench line")
@@ -749,10 +839,15 @@ def main():
     per = {"solve": r["ms_solve"] / npush, "factor": r["ms_factor"] / npush, "env": r["ms_env"] / npush}
     dom = max(per, key=per.get)
     peak, peak_src = peaks()
-    achieved = alg[dom] / (per[dom] * 1e-3) / 1e9
-    kname = {"solve": "level-1 local solve Y = X_(1) B^_1^T",
-             "factor": "level-1 factorisation Q1 = orth(Y)",
-             "env": "level-1 environment E_2 = G_1^T X_(1)"}[dom]
+    ach = {k: alg[k] / (per[k] * 1e-3) / 1e9 for k in per}
+    knames = {"solve": "k_fast_solve: level-1 local solve Y = X_(1) B^_1^T (S4, slice contraction)",
+              "factor": "k_fast_factor: level-1 r x r factor and basis Q1 = orth(Y) (S5)",
+              "env": "k_fast_env1: level-1 environment E_2 = Q1^T X_(1) (S6, slice contraction)"}
+    # the same stream with the FP32 r x r factor (the faster variant, for comparison)
+    r32f = time_arm(args.ingest, args.steps, args.warmup, pool, dist_on, None, factor="fp32")
+    factor_fp32 = {"value": args.steps * world / (r32f["ms"] / 1000.0), "unit": "slices/s",
+                   "ms_per_step": r32f["ms"] / args.steps,
+                   "ms_factor_per_launch": r32f["ms_factor"] / max(1, r32f["npush"]), "re": r32f["re"]}
     # end to end: 8-bit video frames over the host link, widened on the device (the pixels
     # are integers 0..255, exact in FP16); the FP16-frame variant is reported beside it
     wire = "u8" if args.ingest in ("f16", "bf16") else "ingest"
@@ -795,6 +890,9 @@ def main():
             "inputs": f"stream b at step t reads pool frame o_t + b; one push reads {S * slice_bytes / 1e6:.0f} MB",
         }
     c4 = c4_arm(args.c4_steps) if args.c4_steps > 0 else None
+    sensor = None
+    if args.sensor_steps > 0 and world == 1:
+        sensor = {ing: sensor_arm(ing, args.sensor_steps, args.warmup) for ing in ("f32", "bf16")}
     served = serve_arm(args.serve_seconds) if args.serve_seconds > 0 and world == 1 else None
     table1 = table1_arm() if args.table1 and world == 1 else None
     f32 = None
@@ -809,10 +907,34 @@ def main():
                "hbm_gbs": args.steps * world / (r32["ms"] / 1000.0) * int(np.prod(DIMS)) * 4 / 1e9}
         del pool32
     cpu = None
+    checks = {}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        rate, done, threads, spent = cpu_baseline_oracle(args.ingest, budget_s=15.0)
-        cpu = {"value": rate, "unit": "slices/s", "cores": threads, "kind": "oracle",
-               "sample": f"first {done} frames of the same stream ({spent:.1f} s), FP64 literal Algorithm 1"}
+        # the oracle on a bounded prefix of the headline stream, the GPU path in lockstep on the
+        # same frames (FP16 and FP32 ingest share the oracle run: the frames are integers); its
+        # time per slice is the CPU baseline
+        vc = oracle_check("video", DIMS, RANKS, [args.ingest, "f32"], args.oracle_frames)
+        checks["video"] = vc
+        try:
+            from threadpoolctl import threadpool_info
+            threads = max([d.get("num_threads", 1) for d in threadpool_info()] + [1])
+        except Exception:
+            threads = os.cpu_count() or 1
+        cpu = {"value": 1.0 / vc["oracle_s_per_slice"], "unit": "slices/s", "cores": threads, "kind": "oracle",
+               "sample": f"first {vc['frames']} frames of the same stream "
+                         f"({vc['frames'] * vc['oracle_s_per_slice']:.1f} s), FP64 literal Algorithm 1"}
+        if sensor is not None:
+            checks["sensor"] = oracle_check("sensor", SENSOR_DIMS, SENSOR_RANKS, ["f32", "bf16"],
+                                            args.oracle_frames)
+    bat_roof = {}
+    if batched is not None:
+        bro = batched["roofline"]
+        b_alg = S * alg["solve"]
+        bat_roof = {"batched_streams": S,
+                    "batched_solve_frac": bro["achieved_all"]["solve"] / peak,
+                    "batched_env_frac": bro["achieved_all"]["env"] / peak,
+                    "batched_step_gbs_slice_once": batched["hbm_gbs"],
+                    "batched_step_frac_slice_once": batched["hbm_gbs"] / peak}
+        del b_alg
     lat = r["lat"]
     if rank == 0:
         line = {
@@ -820,10 +942,16 @@ def main():
             "warmup": args.warmup, "ms_per_step": r["ms"] / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": args.ingest, "data": "synthetic",
             "config": {"workload": WORKLOAD, "ingest": args.ingest,
-                       "precision": (f"{args.ingest.upper()} ingest, FP32 accumulation and state; basis from an "
-                                     "FP32 scaled Cholesky with an exact projector correction for the rounded "
-                                     "basis; FP64 r x r factor when cores are exported") if args.ingest != "f32" else
+                       "precision": (f"{args.ingest.upper()} ingest, FP32 accumulation and state; FP64 r x r factor "
+                                     "of each local solve's Gram (fraction-free LDL^T, Gram summed in FP64 from FP32 "
+                                     "partials); FP32 tall apply rounded to the ingest type with an exact projector "
+                                     "correction for the rounded basis") if args.ingest != "f32" else
                                     "FP32 ingest and state; Cholesky-QR (FP32 factor, FP64 sums) + FP64 polar pass",
+                       "oracle_check": "; ".join(
+                           f"{k} first {v['frames']} frames: " + ", ".join(
+                               f"{ing} |RE_gpu - RE_oracle| {d['abs_diff_re']:.2e} (RE {d['re_oracle']:.5f}), "
+                               f"max per-slice rel diff {d['max_rel_diff_per_slice']:.2e}"
+                               for ing, d in v["per_ingest"].items()) for k, v in checks.items()),
                        "l2": f"inputs larger than L2: {args.pool}-frame pool "
                              f"({args.pool * slice_bytes / 1e6:.0f} MB), played forward and backward",
                        "parallelism": f"replicas x{world}" if world > 1 else "single stream"},
@@ -832,12 +960,19 @@ def main():
             "latency_ms": {"p50": lat[len(lat) // 2], "p99": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
                            "n": len(lat)},
             "re": r["re"],
-            "roofline": {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": peak,
-                         "peak_source": peak_src, "unit": "GB/s", "frac": achieved / peak,
-                         "traffic": traffic_record(dom),
-                         "algorithmic_bytes": alg[dom], "ms_per_launch": per[dom],
-                         "step_share": per[dom] / (r["ms_push"] / npush),
-                         "ms_per_launch_all": per},
+            "roofline": dict({"bound": "hbm", "kernel": knames["solve"], "achieved": ach["solve"], "peak": peak,
+                              "peak_source": peak_src, "unit": "GB/s", "frac": ach["solve"] / peak,
+                              "traffic": traffic_record("solve"),
+                              "algorithmic_bytes": alg["solve"], "ms_per_launch": per["solve"],
+                              "env_kernel": knames["env"], "env_achieved": ach["env"], "env_frac": ach["env"] / peak,
+                              "env_ms_per_launch": per["env"],
+                              "dominant_kernel": knames[dom], "dominant_achieved": ach[dom],
+                              "dominant_frac": ach[dom] / peak, "dominant_ms_per_launch": per[dom],
+                              "dominant_step_share": per[dom] / (r["ms_push"] / npush),
+                              "factor_ms_per_launch": per["factor"]}, **bat_roof),
+            "factor_fp32": factor_fp32,
+            "sensor": sensor,
+            "oracle_checks": checks,
             "e2e": {"value": args.e2e_steps * world / e2e_sec, "unit": "slices/s",
                     "h2d_bytes_per_step": e2e["h2d"], "d2h_bytes_per_step": e2e["d2h"],
                     "wire": "8-bit pixels, widened to the ingest type on the device (ttals_widen_u8)"

@@ -12,9 +12,17 @@
  *  - Core k (1-based) has shape r_{k-1} x I_k x r_k, C-order, r_0 = 1; core n is
  *    the temporal row g_n of length r_{n-1}.
  *  - Ingest dtype F64 runs every step in FP64.  F32, F16 and BF16 ingest keep
- *    the state in FP32 and contract the slice with FP32 accumulation; each local
- *    solve is orthogonalised by a Gram / Cholesky pass (FP32 factor, FP64 sums)
- *    followed by one FP64 polar re-orthogonalisation.
+ *    the state in FP32 and contract the slice with FP32 accumulation.  How each
+ *    local solve is orthogonalised (Sec. 3.4.2) depends on the path:
+ *     - the fused FP16/BF16 path (saturated second level, r_1 <= 64): the Gram of
+ *       the level-1 solve is summed in FP64 from FP32 partials and factored in
+ *       FP64 (cfg->factor = 0, default; 1 = FP32 factor); the tall apply runs in
+ *       FP32 and is rounded to the ingest type, and the projector is made exact
+ *       for that rounded basis with its own Gram (no polar pass, qr_passes is
+ *       ignored);
+ *     - every other F32/F16/BF16 stream: a Gram / Cholesky pass (FP32 factor,
+ *       FP64 sums), followed, when qr_passes = 2 (the default), by one FP64 polar
+ *       re-orthogonalisation.
  *  - Calls that take a `cuda_stream` only enqueue work on it (NULL = legacy
  *    default stream) and return without synchronising; device-side conditions
  *    (non-finite slice, rank-deficient local solve handled by the Householder
@@ -61,16 +69,20 @@ typedef struct {
     ttals_dtype ingest;  /* dtype of every slice pushed to this stream (default F64)       */
     uint64_t seed;       /* seed of the default random initial cores (default 0x5eed)     */
     int device;          /* CUDA device ordinal (default 0)                               */
-    int qr_passes;       /* orthogonalisation passes per local solve: 1 = Cholesky-QR with an
+    int qr_passes;       /* orthogonalisation passes per local solve on the generic path
+                            (F64/F32 ingest, unsaturated levels): 1 = Cholesky-QR with an
                             FP32 factor only, 2 = followed by one FP64 polar
-                            re-orthogonalisation (0 = default = 2)                        */
+                            re-orthogonalisation (0 = default = 2).  The fused FP16/BF16
+                            path ignores it (see `factor`)                               */
     int env_kernel;      /* fused path, environment kernel (S6): 0 = chosen by shape, 1 = the
                             clustered one, 2 = one CTA per column tile over all rows (ignored
                             when its tile does not fit), 3 = streamed row stages, 4 = streamed
                             row stages on tcgen05 (ranks padded to 16, 32 or 64; else 3)  */
     int k1_split;        /* fused path, k-splits of the local solve (S4): 0 = chosen by
                             shape and batch size, else 1, 2, 4 or 8                         */
-    int reserved[2];     /* must be zero                                                  */
+    int factor;          /* fused path, the r x r factor of each local solve's Gram (S5):
+                            0 = FP64 (default), 1 = FP32 (one warp; faster, for comparison)  */
+    int reserved[1];     /* must be zero                                                  */
 } ttals_config;
 
 /*
@@ -226,8 +238,11 @@ ttals_status ttals_slice_error_noalloc(const void *x_dev, ttals_dtype x_dtype, c
  * independent streams of ONE shape (dims, ranks, ingest) whose updates run in the
  * same kernel launches (each launch's grid gains one plane per stream), so that a
  * step of many small streams reads their slices at full HBM rate.  Every stream of
- * a batch computes exactly what it computes alone: the same kernels, the same
- * reduction orders, bitwise the same results.
+ * a batch performs the arithmetic it performs alone; a batch may take other
+ * kernel schedules (whole-row tcgen05 tiles, fewer k-splits, streamed row stages),
+ * so its FP32 sums can run in another order: results agree to FP32 rounding after
+ * one step, and the 16-bit state can then round differently (a stream's results do
+ * not depend on its slot or on the other streams of the batch, bit for bit).
  *
  * ttals_create_batch - like ttals_create, for 1 <= n_streams <= TTALS_MAX_BATCH
  *   streams.  Stream b starts from its own default cores (the b-th draw of the

@@ -184,6 +184,7 @@ struct ttals_stream {
   unsigned long long active_mask = ~0ull;   // streams of a batch that take the next push
   int cfg_env_kernel = 0;             // ttals_config.env_kernel (0: by shape)
   int cfg_k1_split = 0;               // ttals_config.k1_split (0: by shape and batch)
+  int cfg_factor = 0;                 // ttals_config.factor (0: FP64 r x r factor, 1: FP32)
   size_t bytes = 0;
   std::vector<void*> allocs;
   unsigned long long nlaunch = 0;      // kernels launched by this stream (host counter)
@@ -431,8 +432,9 @@ struct Impl final : ttals_stream {
     const int r = rk(1);
     if (J % 8 != 0 || r > 64 || M > 8 * 512) return TTALS_OK;
     np_ = ((r + 15) / 16) * 16;
-    // the factor cluster holds 1/8 of Y and Q1 per CTA in shared memory (plus ~37 KB static)
-    if (fast::k1b_smem_bytes((int)M, r, np_) + 40 * 1024 > 227 * 1024) {
+    // the factor cluster holds 1/8 of Y and Q1 per CTA in shared memory (plus its static
+    // shared memory, fast::K1B_STATIC_SMEM)
+    if (fast::k1b_smem_bytes((int)M, r, np_) + fast::K1B_STATIC_SMEM > 227 * 1024) {
       np_ = 16;
       return TTALS_OK;
     }
@@ -689,10 +691,11 @@ struct Impl final : ttals_stream {
       ab.hh_work = fHH;
       ab.Qfb = fQfb;
       ab.ctl = ctl_base;
+      ab.fp64 = cfg_factor == 0 ? 1 : 0;
       std::memcpy(ab.zmap, zact, sizeof(zact));
       // clusters of 8 one-CTA-per-SM CTAs fit the GPCs for up to 8 streams at once; beyond
       // that clusters of 4 (twice the rows per CTA) keep the step in one wave
-      const int kbc = (n_act > 8 && fast::k1b_smem_bytes((int)dims[0], r, NP, 4) + 40 * 1024 <= 227 * 1024) ? 4 : 8;
+      const int kbc = (n_act > 8 && fast::k1b_smem_bytes((int)dims[0], r, NP, 4) + fast::K1B_STATIC_SMEM <= 227 * 1024) ? 4 : 8;
       cudaLaunchAttribute atb[2];
       atb[0] = at[0];
       atb[0].val.clusterDim.y = (unsigned)kbc;
@@ -1266,8 +1269,8 @@ static ttals_status create_streams(int nbatch, int n_slice_modes, const int64_t*
   c.device = 0;
   if (cfg) {
     c = *cfg;
-    for (int i = 0; i < 2; ++i)
-      if (c.reserved[i] != 0) return TTALS_EINVAL;
+    if (c.reserved[0] != 0) return TTALS_EINVAL;
+    if (c.factor != 0 && c.factor != 1) return TTALS_EINVAL;
     if (c.env_kernel < 0 || c.env_kernel > 4) return TTALS_EINVAL;
     if (c.k1_split != 0 && c.k1_split != 1 && c.k1_split != 2 && c.k1_split != 4 && c.k1_split != 8)
       return TTALS_EINVAL;
@@ -1325,6 +1328,7 @@ static ttals_status create_streams(int nbatch, int n_slice_modes, const int64_t*
   s->nbatch = nbatch;
   s->cfg_env_kernel = c.env_kernel;
   s->cfg_k1_split = c.k1_split;
+  s->cfg_factor = c.factor;
   if (cudaEventCreateWithFlags(&s->ev, cudaEventDisableTiming) != cudaSuccess) {
     delete s;
     return TTALS_ECUDA;

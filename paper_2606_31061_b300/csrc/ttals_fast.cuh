@@ -23,6 +23,7 @@
 #include <cuda.h>
 
 #include "ttals_kernels.cuh"
+#include "ttals_r64.cuh"
 
 namespace ttals {
 namespace fast {
@@ -806,6 +807,9 @@ __global__ void __launch_bounds__(K1T_THREADS, 1)
 // takes the FP64 Householder QR of Y on rank 0 instead.
 constexpr int K1B_THREADS = 256;
 constexpr int KB_CLUSTER = 8;       // the largest factor cluster: W2-partial slab stride
+// static shared memory of k_fast_factor (W1 as float + its rounding error, L^T, the FP64
+// factor's columns, small arrays), rounded up; the launch checks dynamic + static <= 227 KB
+constexpr int K1B_STATIC_SMEM = 60 * 1024;
 
 struct FactorArgs {
   const float* Y;         // M x r
@@ -817,6 +821,7 @@ struct FactorArgs {
   double* hh_work;        // 2*M*r doubles (fallback)
   float* Qfb;             // M x r (fallback Q, float)
   Ctl* ctl;
+  int fp64;               // 1: the r x r factor in FP64 (r64::ldl_factor), 0: FP32 (one warp)
   unsigned char zmap[64];      // grid plane blockIdx.z -> stream (slot) of the batch
 };
 
@@ -850,7 +855,9 @@ __global__ void __launch_bounds__(K1B_THREADS, 1) k_fast_factor(FactorArgs a0) {
   extern __shared__ __align__(16) unsigned char smem[];
   constexpr int LDY = NP + 4, LQ = NP + 8, LDT = NP + 4;
   constexpr int NB = NP / 4, NBLK = NB * NB, NRG = k1b_rgroups(NP);
-  __shared__ float W[64 * 64];             // W1, then W2 (r x r)
+  __shared__ float W[64 * 64];             // W1 (FP32 rounding of its float-float sum)
+  __shared__ float Wlo[64 * 64];           // W1 - W exactly: W1 = W + Wlo (the FP64 factor's input)
+  __shared__ r64::Smem ldlsm;
   __shared__ __align__(16) float LT[64 * 68];   // L^T: LT[k*LDT + i] = L[i][k] (zero above)
   __shared__ float dsc[64];
   __shared__ float invd[64];               // 1 / L[i][i]
@@ -959,7 +966,11 @@ __global__ void __launch_bounds__(K1B_THREADS, 1) k_fast_factor(FactorArgs a0) {
         float hi = 0.f, lo = 0.f;
 #pragma unroll
         for (int q = 0; q < KBC; ++q) two_sum_acc(hi, lo, v[u][q]);
-        if (e0 + u * K1B_THREADS < rr) W[e0 + u * K1B_THREADS] = hi + lo;
+        if (e0 + u * K1B_THREADS < rr) {
+          const float w = hi + lo;
+          W[e0 + u * K1B_THREADS] = w;
+          Wlo[e0 + u * K1B_THREADS] = (hi - w) + lo;     // exact (|lo| <= ulp(hi) / 2)
+        }
       }
     }
   }
@@ -988,7 +999,19 @@ __global__ void __launch_bounds__(K1B_THREADS, 1) k_fast_factor(FactorArgs a0) {
   // ---- 2. Cholesky of the scaled Gram: D W1 D = L L^T, stored transposed (LT)
   for (int e = tid; e < NP * LDT; e += K1B_THREADS) LT[e] = 0.f;
   __syncthreads();
-  if (!flags[1]) {
+  if (!flags[1] && a.fp64) {
+    // FP64: W1 = W + Wlo (its float-float sum) scaled by D; a scaled pivot D_k <= 1e-8 (the
+    // local solve's columns nearly dependent: condition number above ~1e4) takes the
+    // Householder path, as does a failed FP32 factor below
+    const auto load = [&](int i, int j) -> double {
+      return ((double)W[i * r + j] + (double)Wlo[i * r + j]) * (double)dsc[i] * (double)dsc[j];
+    };
+    if (tid < 128) {
+      const bool ok = r64::ldl_factor<128>(r, load, 1e-8, ldlsm, LT, LDT, invd, nullptr, 0);
+      if (!ok && tid == 0) flags[1] = 1;
+    }
+    __syncthreads();
+  } else if (!flags[1]) {
     if constexpr (NP <= 32) {
       if (warp == 0) {
         float l[32];

@@ -1,0 +1,147 @@
+// ttals_r64.cuh - FP64 r x r factorisation for the per-slice update (Sec. 3.4.2: the QR of the
+// local solve G~_k = Q R, computed as the Cholesky factor of its Gram matrix: G~^T G~ = R^T R).
+//
+// B300's FP64 unit is narrow and slow to answer (measured on this part: a dependent DFMA takes
+// 64 cycles; one warp issues 0.5 DFMA per clock, a whole SM 1.7).  A textbook Cholesky puts a
+// square root or a reciprocal and a block barrier on the critical path of each of the r pivot
+// steps, which made a first CTA version take 20 us at r = 32.  This one keeps the chain of a
+// pivot step to one multiply, one fused multiply-add and one barrier:
+//
+//  * Fraction-free elimination (no division): step k replaces every trailing entry by
+//      A_ij <- 2^-e (d A_ij - A_ik A_jk),  d = A_kk = c 2^e,  c in [1, 2),
+//    i.e. A_ij <- c A_ij - 2^-e (A_ik A_jk).  The power of two 2^-e keeps the entries bounded:
+//    with S^(k) the true Schur complements, A^(k) = P_k S^(k), P_k = c_0 c_1 ... c_{k-1}, and
+//    every c_j lies in [1, 2).  The scaling by 2^-e is an exact exponent change.
+//  * The Cholesky factor follows without any division on the critical path:
+//      D_k = A^(k)_kk / P_k,   L_ik = A^(k)_ik / sqrt(A^(k)_kk P_k).
+//  * Each thread keeps its entries of the lower triangle in registers, ordered by column
+//    from the last, so the entries still to be updated at step k are a prefix of the order;
+//    column k+1 is published through a double-buffered shared-memory column, one barrier per
+//    step.  Four warps (one per SM sub-partition: the FP64 rate is per sub-partition) do the
+//    work and synchronise through a named barrier.
+//
+// Used by the fused path's factor kernel (every CTA of the factor cluster factors the scaled
+// Gram D W1 D of the level-1 local solve) and by the batched FP64 kernel k_r64_factor.
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace r64 {
+
+constexpr int kMaxR = 64;
+
+struct Smem {
+  double col[2][kMaxR];   // column k (parity k) of the current elimination step
+  double dk[kMaxR];       // A^(k)_kk
+  double pk[kMaxR];       // P_k
+  double rs[kMaxR];       // 1 / sqrt(A^(k)_kk P_k)
+  int bad;
+};
+
+// d > 0, normal:  d = c 2^e with c in [1, 2) (exact)
+__device__ __forceinline__ void pow2_split(double d, double& c, int& e) {
+  const int hi = __double2hiint(d), lo = __double2loint(d);
+  e = ((hi >> 20) & 0x7ff) - 1023;
+  c = __hiloint2double((hi & 0x800fffff) | (1023 << 20), lo);
+}
+
+// t 2^-e by an exponent change, without a branch: exact for normal t whose result stays
+// normal; a zero or subnormal t, or a result below the normal range, gives 0 (its share of an
+// update is below 2^-1000 relative), a non-finite t stays non-finite (the pivot test then fails)
+__device__ __forceinline__ double times_pow2(double t, int e) {
+  const int hi = __double2hiint(t), lo = __double2loint(t);
+  const int eb = (hi >> 20) & 0x7ff;
+  const int nb = eb - e;
+  const double moved = __hiloint2double(hi - e * (1 << 20), lo);
+  const double scaled = (eb != 0 && nb >= 1 && nb <= 2046) ? moved : 0.0;
+  return eb == 0x7ff ? t : scaled;
+}
+
+__device__ __forceinline__ void bar_sync_named(int id, int nthreads) {
+  asm volatile("bar.sync %0, %1;\n" ::"r"(id), "r"(nthreads) : "memory");
+}
+
+// Cholesky factor L of the r x r symmetric matrix S (r <= 64) by threads 0..NT-1 of a CTA
+// (NT a multiple of 32; all of them must call it, the other threads must not).  They
+// synchronise among themselves with named barrier 1; the caller synchronises the rest of the
+// block afterwards.  load(i, j) returns S_ij for i >= j.
+// Writes L (FP32) transposed, LT[k * ldt + i] = L_ik for i >= k (entries above are not
+// touched), invd[k] = 1 / L_kk (FP32) and, if L64 != nullptr, L in FP64 (L64[i * ld64 + k]).
+// Returns false (the same value in every calling thread) when a pivot D_k = S^(k)_kk is not
+// above tol (S not numerically positive definite); the outputs are then unspecified.
+template <int NT, typename Load>
+__device__ bool ldl_factor(int r, Load load, double tol, Smem& sm, float* LT, int ldt, float* invd, double* L64,
+                           int ld64) {
+  constexpr int MAXM = (kMaxR * (kMaxR + 1) / 2 + NT - 1) / NT;
+  const int tid = threadIdx.x;
+  const int N = r * (r + 1) / 2;
+  double a[MAXM];
+  int ii[MAXM], jj[MAXM];
+#pragma unroll
+  for (int m = 0; m < MAXM; ++m) {
+    const int e = tid + m * NT;
+    ii[m] = 0;
+    jj[m] = -1;
+    a[m] = 0.0;
+    if (e < N) {
+      // columns from the last: column j = r-1-q holds entries e in [q(q+1)/2, (q+1)(q+2)/2)
+      int q = (int)((sqrtf(8.f * (float)e + 1.f) - 1.f) * 0.5f);
+      while (q > 0 && q * (q + 1) / 2 > e) --q;
+      while ((q + 1) * (q + 2) / 2 <= e) ++q;
+      const int j = r - 1 - q, i = j + (e - q * (q + 1) / 2);
+      ii[m] = i;
+      jj[m] = j;
+      a[m] = load(i, j);
+      if (j == 0) sm.col[0][i] = a[m];
+    }
+  }
+  if (tid == 0) sm.bad = 0;
+  bar_sync_named(1, NT);
+  double P = 1.0;
+  for (int k = 0; k < r; ++k) {
+    const double* cb = sm.col[k & 1];
+    double* nb = sm.col[(k + 1) & 1];
+    const double d = cb[k];
+    if (tid == 0) {
+      sm.dk[k] = d;
+      sm.pk[k] = P;
+    }
+    double c = 1.0;
+    int ex = 0;
+    if (d > 0.0 && d < 1.0e300) pow2_split(d, c, ex);   // else: plain step, the pivot test fails below
+    const int nact = (r - k - 1) * (r - k) / 2;         // entries of columns > k: a prefix
+#pragma unroll
+    for (int m = 0; m < MAXM; ++m) {
+      if (m * NT < nact) {
+        const bool act = tid + m * NT < nact;
+        const double t = cb[act ? ii[m] : 0] * cb[act ? jj[m] : 0];
+        const double v = fma(c, a[m], -times_pow2(t, ex));
+        a[m] = act ? v : a[m];
+        if (act && jj[m] == k + 1) nb[ii[m]] = v;
+      }
+    }
+    P *= c;
+    bar_sync_named(1, NT);
+  }
+  if (tid < r) {
+    const double dd = sm.dk[tid], pp = sm.pk[tid];
+    const bool ok = dd > tol * pp;                       // D_k = dd / pp > tol (pp >= 1)
+    sm.rs[tid] = ok ? rsqrt(dd * pp) : 0.0;
+    if (!ok) sm.bad = 1;
+    if (invd) invd[tid] = ok ? (float)(pp * sm.rs[tid]) : 0.f;
+  }
+  bar_sync_named(1, NT);
+#pragma unroll
+  for (int m = 0; m < MAXM; ++m) {
+    if (jj[m] >= 0) {
+      const double l = a[m] * sm.rs[jj[m]];
+      if (LT) LT[jj[m] * ldt + ii[m]] = (float)l;
+      if (L64) L64[ii[m] * ld64 + jj[m]] = l;
+    }
+  }
+  const bool ok = sm.bad == 0;
+  bar_sync_named(1, NT);
+  return ok;
+}
+
+}  // namespace r64

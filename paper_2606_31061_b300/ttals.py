@@ -40,7 +40,7 @@ class TTALSError(RuntimeError):
 class Config(ctypes.Structure):
     _fields_ = [("ingest", ctypes.c_int), ("seed", ctypes.c_uint64), ("device", ctypes.c_int),
                 ("qr_passes", ctypes.c_int), ("env_kernel", ctypes.c_int), ("k1_split", ctypes.c_int),
-                ("reserved", ctypes.c_int * 2)]
+                ("factor", ctypes.c_int), ("reserved", ctypes.c_int * 1)]
 
 
 _lib = None
@@ -117,11 +117,14 @@ class Stream:
 
     def __init__(self, dims: Sequence[int], ranks: Sequence[int], ingest: str = "f64",
                  seed: int = 0x5EED, device: int = 0, qr_passes: int = 0, n_streams: int = 0,
-                 env_kernel: int = 0, k1_split: int = 0):
+                 env_kernel: int = 0, k1_split: int = 0, factor: str = "fp64"):
         lib = load()
         self.dims = tuple(int(d) for d in dims)
         self.ingest = ingest
-        cfg = Config(DTYPES[ingest], seed, device, qr_passes, env_kernel, k1_split, (ctypes.c_int * 2)(0, 0))
+        if factor not in ("fp64", "fp32"):
+            raise ValueError(f"factor must be 'fp64' or 'fp32', not {factor!r}")
+        cfg = Config(DTYPES[ingest], seed, device, qr_passes, env_kernel, k1_split, 0 if factor == "fp64" else 1,
+                     (ctypes.c_int * 1)(0))
         h = ctypes.c_void_p()
         if n_streams > 0:
             code = lib.ttals_create_batch(int(n_streams), len(self.dims), _i64(self.dims), _i64(ranks),

@@ -117,7 +117,7 @@ def test_group_mixed_shapes_match_alone():
             alone.reconstruct(out, "f64")
             xa = out.cpu().numpy()
             rel = np.linalg.norm(xs[i][t] - xa) / np.linalg.norm(xa)
-            assert rel <= 1e-3, (i, t, rel)
+            assert rel <= (1e-5 if t == 0 else 1e-3), (i, t, rel)
         sa, sg = np.array(alone.stats()), grp.stats(i)
         assert abs(np.sqrt(sa[3] / sa[2]) - np.sqrt(sg[3] / sg[2])) <= 1e-3
         assert grp.step_count(i) == T

@@ -320,3 +320,28 @@ def test_argument_errors():
     with pytest.raises(TTALSError):       # misaligned pointer
         T._check(T.load().ttals_push_slice(st._h, T.ctypes.c_void_p(y.data_ptr() + 4), T.F32, None), "push")
     assert st.step() == 0
+
+
+@pytest.mark.parametrize("factor", ["fp64", "fp32"])
+def test_fused_factor_precisions(factor):
+    """The fused FP16 path with its FP64 r x r factor (the default) and with the FP32 factor
+    (the faster variant): both within the FP16 ingest bar of the oracle, on a video-shaped
+    stream and on a rank-64 square stream (the factor's largest size)."""
+    from paper_2606_31061_b300.ttals import Stream
+    torch = _torch()
+    for name, kw in (("video", {"dims": (120, 160, 3)}), ("square", {"s": 256, "r": 64})):
+        sp = synth.make_stream(name, **kw)
+        r = O.clamp_ranks(sp.dims, sp.ranks)
+        cores, g = synth.init_cores(sp.dims, r, seed=7)
+        st = Stream(sp.dims, sp.ranks, ingest="f16", factor=factor)
+        st.set_cores(cores, g)
+        orc = O.OnlineTTALS(sp.dims, r, cores, g)
+        xs, xo = [], []
+        for x in sp.take(10):
+            dx, exact = _upload(x, "f16")
+            st.push(dx)
+            xs.append(exact)
+            xo.append(orc.step(exact))
+        s = st.stats()
+        re_o = O.stream_relative_error(xs, xo)
+        assert abs(np.sqrt(s[3] / s[2]) - re_o) <= 1e-3, (name, factor, np.sqrt(s[3] / s[2]), re_o)
