@@ -1000,14 +1000,16 @@ __global__ void __launch_bounds__(K1B_THREADS, 1) k_fast_factor(FactorArgs a0) {
   for (int e = tid; e < NP * LDT; e += K1B_THREADS) LT[e] = 0.f;
   __syncthreads();
   if (!flags[1] && a.fp64) {
-    // FP64: W1 = W + Wlo (its float-float sum) scaled by D; a scaled pivot D_k <= 1e-8 (the
-    // local solve's columns nearly dependent: condition number above ~1e4) takes the
-    // Householder path, as does a failed FP32 factor below
+    // FP64: W1 = W + Wlo (its float-float sum) scaled by D.  A scaled pivot D_k <= 1e-4 takes
+    // the Householder path, as in the FP32 factor below: the threshold is set by the FP32 tall
+    // apply z = L^{-1} (D y), whose rows each see their own rounding of L^{-1}, so that the
+    // span of Q1 drifts from span(Y) by about 6e-8 cond(Y) (measured: a 1e-8 threshold let
+    // streams through whose RE moved by 1e-3 from the oracle's)
     const auto load = [&](int i, int j) -> double {
       return ((double)W[i * r + j] + (double)Wlo[i * r + j]) * (double)dsc[i] * (double)dsc[j];
     };
     if (tid < 128) {
-      const bool ok = r64::ldl_factor<128>(r, load, 1e-8, ldlsm, LT, LDT, invd, nullptr, 0);
+      const bool ok = r64::ldl_factor<128, NP>(r, load, 1e-4, ldlsm, LT, LDT, invd, nullptr, 0);
       if (!ok && tid == 0) flags[1] = 1;
     }
     __syncthreads();

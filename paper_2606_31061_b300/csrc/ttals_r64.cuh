@@ -38,11 +38,15 @@ struct Smem {
   int bad;
 };
 
-// d > 0, normal:  d = c 2^e with c in [1, 2) (exact)
+// d = c 2^e with c in [1, 2) (exact) for a positive normal d below 2^1022; any other d (zero,
+// negative, subnormal, huge, non-finite) gives c = 1, e = 0 (a plain step, which the pivot test
+// rejects).  Integer operations only: on this part every FP64-pipe instruction, a compare or a
+// conversion included, costs a warp ~64 cycles of issue.
 __device__ __forceinline__ void pow2_split(double d, double& c, int& e) {
   const int hi = __double2hiint(d), lo = __double2loint(d);
-  e = ((hi >> 20) & 0x7ff) - 1023;
-  c = __hiloint2double((hi & 0x800fffff) | (1023 << 20), lo);
+  const bool ok = hi >= 0x00100000 && hi < 0x7fd00000;
+  e = ok ? ((hi >> 20) & 0x7ff) - 1023 : 0;
+  c = ok ? __hiloint2double((hi & 0x000fffff) | (1023 << 20), lo) : 1.0;
 }
 
 // t 2^-e by an exponent change, without a branch: exact for normal t whose result stays
@@ -61,7 +65,7 @@ __device__ __forceinline__ void bar_sync_named(int id, int nthreads) {
   asm volatile("bar.sync %0, %1;\n" ::"r"(id), "r"(nthreads) : "memory");
 }
 
-// Cholesky factor L of the r x r symmetric matrix S (r <= 64) by threads 0..NT-1 of a CTA
+// Cholesky factor L of the r x r symmetric matrix S (r <= RMAX <= 64) by threads 0..NT-1 of a CTA
 // (NT a multiple of 32; all of them must call it, the other threads must not).  They
 // synchronise among themselves with named barrier 1; the caller synchronises the rest of the
 // block afterwards.  load(i, j) returns S_ij for i >= j.
@@ -69,10 +73,14 @@ __device__ __forceinline__ void bar_sync_named(int id, int nthreads) {
 // touched), invd[k] = 1 / L_kk (FP32) and, if L64 != nullptr, L in FP64 (L64[i * ld64 + k]).
 // Returns false (the same value in every calling thread) when a pivot D_k = S^(k)_kk is not
 // above tol (S not numerically positive definite); the outputs are then unspecified.
-template <int NT, typename Load>
+template <int NT, int RMAX, typename Load>
 __device__ bool ldl_factor(int r, Load load, double tol, Smem& sm, float* LT, int ldt, float* invd, double* L64,
                            int ld64) {
-  constexpr int MAXM = (kMaxR * (kMaxR + 1) / 2 + NT - 1) / NT;
+  static_assert(RMAX <= kMaxR, "r x r factor up to 64");
+  static_assert(NT >= 32 && NT % 32 == 0, "whole warps, warp 0 among them");
+  // entries per thread for the largest r of this instantiation (the loops are unrolled over
+  // them: a tight bound keeps the code, and the instruction cache misses, small)
+  constexpr int MAXM = (RMAX * (RMAX + 1) / 2 + NT - 1) / NT;
   const int tid = threadIdx.x;
   const int N = r * (r + 1) / 2;
   double a[MAXM];
@@ -97,18 +105,14 @@ __device__ bool ldl_factor(int r, Load load, double tol, Smem& sm, float* LT, in
   }
   if (tid == 0) sm.bad = 0;
   bar_sync_named(1, NT);
-  double P = 1.0;
   for (int k = 0; k < r; ++k) {
     const double* cb = sm.col[k & 1];
     double* nb = sm.col[(k + 1) & 1];
     const double d = cb[k];
-    if (tid == 0) {
-      sm.dk[k] = d;
-      sm.pk[k] = P;
-    }
-    double c = 1.0;
-    int ex = 0;
-    if (d > 0.0 && d < 1.0e300) pow2_split(d, c, ex);   // else: plain step, the pivot test fails below
+    if (tid == 0) sm.dk[k] = d;
+    double c;
+    int ex;
+    pow2_split(d, c, ex);
     const int nact = (r - k - 1) * (r - k) / 2;         // entries of columns > k: a prefix
 #pragma unroll
     for (int m = 0; m < MAXM; ++m) {
@@ -120,12 +124,29 @@ __device__ bool ldl_factor(int r, Load load, double tol, Smem& sm, float* LT, in
         if (act && jj[m] == k + 1) nb[ii[m]] = v;
       }
     }
-    P *= c;
     bar_sync_named(1, NT);
   }
+  // P_k = c_0 ... c_{k-1}, once: an exclusive product scan over the pivots' c (two per lane)
+  if (tid < 32) {
+    double c0 = 1.0, c1 = 1.0;
+    int e_;
+    if (2 * tid < r) pow2_split(sm.dk[2 * tid], c0, e_);
+    if (2 * tid + 1 < r) pow2_split(sm.dk[2 * tid + 1], c1, e_);
+    double incl = c0 * c1;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const double v = __shfl_up_sync(0xffffffffu, incl, o);
+      if (tid >= o) incl *= v;
+    }
+    double excl = __shfl_up_sync(0xffffffffu, incl, 1);
+    if (tid == 0) excl = 1.0;
+    if (2 * tid < kMaxR) sm.pk[2 * tid] = excl;
+    if (2 * tid + 1 < kMaxR) sm.pk[2 * tid + 1] = excl * c0;
+  }
+  bar_sync_named(1, NT);
   if (tid < r) {
     const double dd = sm.dk[tid], pp = sm.pk[tid];
-    const bool ok = dd > tol * pp;                       // D_k = dd / pp > tol (pp >= 1)
+    const bool ok = dd > tol * pp;                       // D_k = dd / pp > tol (pp >= 1; false for NaN)
     sm.rs[tid] = ok ? rsqrt(dd * pp) : 0.0;
     if (!ok) sm.bad = 1;
     if (invd) invd[tid] = ok ? (float)(pp * sm.rs[tid]) : 0.f;

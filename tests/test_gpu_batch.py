@@ -4,11 +4,13 @@
   a pipeline in the environment kernel, fewer k-splits of the solve), a lone stream the ones
   tuned for latency, so the two agree to FP32 summation order, not bitwise.  Checked per
   stream: the first step (same state, same slice: only the order of FP32 sums differs)
-  within 1e-5 relative, the FP32 bar; later steps within 1e-3 relative, because the state
-  operand of the next local solve is carried in the ingest type and an FP32-order
-  difference can round one of its entries the other way (2^-11 relative: measured growth
-  about 5e-5 per step); the relative reconstruction error (RE, Sec. 5.1) within 1e-3
-  absolute (the FP16 ingest bar against the FP64 oracle).
+  within 1e-4 relative; later steps within 1e-3 relative.  An FP32-order difference alone
+  is ~1e-6 here, but the basis Q1 is rounded to the ingest type before the environment pass
+  and the state operand of the next local solve is carried in it, so a difference near a
+  rounding boundary flips an entry by 2^-11 relative: measured 0.2-3e-5 after one step
+  (3e-5 for 16 full-size video streams), growing about 5e-5 per step.  The relative
+  reconstruction error (RE, Sec. 5.1) within 1e-3 absolute (the FP16 ingest bar against
+  the FP64 oracle).
 * In the mix: a stream's results do not depend on its slot or on the other streams' data,
   bit for bit (same batch size, permuted slots, one stream replaced).
 """
@@ -93,7 +95,7 @@ def test_batch_matches_alone(name, kw):
         for t in range(T):
             rel = np.linalg.norm(xb[t] - xa[t]) / max(np.linalg.norm(xa[t]), 1e-300)
             worst.append((t, rel))
-            assert rel <= (1e-5 if t == 0 else 1e-3), (name, b, t, rel)
+            assert rel <= (1e-4 if t == 0 else 1e-3), (name, b, t, rel)
         re_a = np.sqrt(sa[-1][3] / sa[-1][2])
         re_b = np.sqrt(sb[-1][3] / sb[-1][2])
         assert abs(re_a - re_b) <= 1e-3, (name, b, re_a, re_b)
@@ -111,7 +113,7 @@ def test_batch_full_size_video():
         xa, sa = _run_alone(torch, dims, ranks, s[2], s[3], s[4])
         for t in range(T):
             rel = np.linalg.norm(batch[b][0][t] - xa[t]) / np.linalg.norm(xa[t])
-            assert rel <= (1e-5 if t == 0 else 1e-3), (b, t, rel)
+            assert rel <= (1e-4 if t == 0 else 1e-3), (b, t, rel)
 
 
 @pytest.mark.parametrize("name,kw", SHAPES[:2])
@@ -163,7 +165,7 @@ def test_batch_tcgen05_solve_matches_alone(monkeypatch):
             xa, sa = _run_alone(torch, dims, ranks, s[2], s[3], s[4])
             for t in range(4):
                 rel = np.linalg.norm(batch[b][0][t] - xa[t]) / np.linalg.norm(xa[t])
-                assert rel <= (1e-5 if t == 0 else 1e-3), (name, b, t, rel)
+                assert rel <= (1e-4 if t == 0 else 1e-3), (name, b, t, rel)
         monkeypatch.setenv("TTALS_SOLVE_KERNEL", "tc")
 
 
@@ -184,4 +186,4 @@ def test_batch_16_video_streams_full_size():
         xa, sa = _run_alone(torch, dims, ranks, *streams[b])
         for t in range(T):
             rel = np.linalg.norm(batch[b][0][t] - xa[t]) / np.linalg.norm(xa[t])
-            assert rel <= (1e-5 if t == 0 else 1e-3), (b, t, rel)
+            assert rel <= (1e-4 if t == 0 else 1e-3), (b, t, rel)

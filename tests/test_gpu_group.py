@@ -5,7 +5,7 @@
   slices at other steps).
 * Every stream of a mixed-shape group, with the autotuner's schedules, agrees with the same
   stream alone within the FP16 ingest tolerance (RE within 1e-3 absolute, each reconstructed
-  slice within 1e-3 relative).
+  slice within 1e-3 relative; the first step within 1e-4, see test_gpu_batch).
 * Replaying a captured CUDA graph of two steps gives bitwise the steps run eagerly.
 """
 import numpy as np
@@ -117,7 +117,7 @@ def test_group_mixed_shapes_match_alone():
             alone.reconstruct(out, "f64")
             xa = out.cpu().numpy()
             rel = np.linalg.norm(xs[i][t] - xa) / np.linalg.norm(xa)
-            assert rel <= (1e-5 if t == 0 else 1e-3), (i, t, rel)
+            assert rel <= (1e-4 if t == 0 else 1e-3), (i, t, rel)
         sa, sg = np.array(alone.stats()), grp.stats(i)
         assert abs(np.sqrt(sa[3] / sa[2]) - np.sqrt(sg[3] / sg[2])) <= 1e-3
         assert grp.step_count(i) == T
