@@ -708,6 +708,51 @@ def oracle_check(name, dims, ranks, ingests, nframes, init_seed=7, **kw):
     return {"frames": nframes, "per_ingest": res, "oracle_s_per_slice": orc_s / max(1, orc_n)}
 
 
+def ablation_arm(T=500, dims=(60, 80, 3), ranks=(30, 3, 3)):
+    """Sec. 5.4 ablation (Table ablation_ortho): the relative error of the stream so far at
+    t = 10, 100, 500 with orthogonalisation (literal) and without it (noortho: LQ/QR removed,
+    Gram-inverse local solves), on the GPU in FP64 and FP32 ingest and in the oracle, for a
+    colour-video-shaped stream with the paper's ranks (30,3,3) (synthetic stand-in for the
+    paper's continuousPan sequence, which is not available)."""
+    import torch
+    from oracle import ttals_oracle as O
+    from paper_2606_31061_b300 import synth
+    from paper_2606_31061_b300.ttals import Stream
+    sp = synth.make_stream("video", dims=dims)
+    frames = sp.take(T)
+    r = O.clamp_ranks(dims, ranks)
+    cores, g = synth.init_cores(dims, r, seed=7)
+    marks = (10, 100, 500)
+    out = {}
+    for mode in ("literal", "noortho"):
+        for ingest in ("f64", "f32"):
+            st = Stream(dims, ranks, ingest=ingest, mode=mode)
+            st.set_cores(cores, g)
+            dt = torch.float64 if ingest == "f64" else torch.float32
+            curve = {}
+            for t, x in enumerate(frames, 1):
+                st.push(torch.from_numpy(x).to(dt).cuda())
+                if t in marks:
+                    s_ = st.stats()
+                    curve[t] = math.sqrt(s_[3] / s_[2])
+            st.close()
+            out[f"gpu_{ingest}_{mode}"] = curve
+        orc = O.OnlineTTALS(dims, r, cores, g, mode=mode)
+        num = den = 0.0
+        curve = {}
+        for t, x in enumerate(frames, 1):
+            xh = orc.step(x)
+            num += float(np.sum((x - xh) ** 2))
+            den += float(np.sum(x * x))
+            if t in marks:
+                curve[t] = math.sqrt(num / den)
+        out[f"oracle_{mode}"] = curve
+    return {"workload": f"colour-video-shaped stream {dims[0]}x{dims[1]}x{dims[2]}, ranks {ranks}, T = {T}",
+            "re_at_t": out,
+            "paper_continuousPan": {"w/o Ortho": {10: 0.097, 100: 0.147, 500: 0.203},
+                                    "w/ Ortho": {10: 0.097, 100: 0.100, 500: 0.100}}}
+
+
 def cpu_baseline_oracle(ingest, budget_s=15.0, max_steps=None):
     """The FP64 oracle (test infrastructure) on the host cores, on a bounded prefix of the
     same stream: returns (slices/s, steps, threads, seconds)."""
@@ -789,6 +834,7 @@ def main():
     ap.add_argument("--serve-seconds", type=float, default=2.0, help="serving-loop traffic (0: skip)")
     ap.add_argument("--table1", type=int, default=1, help="high-order scalability arm (0: skip)")
     ap.add_argument("--sensor-steps", type=int, default=300, help="sensor-shaped stream arm (0: skip)")
+    ap.add_argument("--ablation", type=int, default=1, help="Sec. 5.4 orthogonality ablation arm (0: skip)")
     ap.add_argument("--oracle-frames", type=int, default=40,
                     help="prefix on which the oracle is timed and compared with the GPU path")
     ap.add_argument("--profile-case", default=None, choices=["single", "batched"],
@@ -890,6 +936,7 @@ def main():
             "inputs": f"stream b at step t reads pool frame o_t + b; one push reads {S * slice_bytes / 1e6:.0f} MB",
         }
     c4 = c4_arm(args.c4_steps) if args.c4_steps > 0 else None
+    ablation = ablation_arm() if args.ablation and world == 1 else None
     sensor = None
     if args.sensor_steps > 0 and world == 1:
         sensor = {ing: sensor_arm(ing, args.sensor_steps, args.warmup) for ing in ("f32", "bf16")}
@@ -972,6 +1019,7 @@ def main():
                               "factor_ms_per_launch": per["factor"]}, **bat_roof),
             "factor_fp32": factor_fp32,
             "sensor": sensor,
+            "ablation_ortho": ablation,
             "oracle_checks": checks,
             "e2e": {"value": args.e2e_steps * world / e2e_sec, "unit": "slices/s",
                     "h2d_bytes_per_step": e2e["h2d"], "d2h_bytes_per_step": e2e["d2h"],

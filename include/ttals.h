@@ -82,7 +82,12 @@ typedef struct {
                             shape and batch size, else 1, 2, 4 or 8                         */
     int factor;          /* fused path, the r x r factor of each local solve's Gram (S5):
                             0 = FP64 (default), 1 = FP32 (one warp; faster, for comparison)  */
-    int reserved[1];     /* must be zero                                                  */
+    int mode;            /* local solves: 0 = literal (Eq. proposed-core-update under the
+                            orthogonality of Sec. 3.3; default), 1 = lsq (the Gram form of
+                            Sec. 3.3: G~_k = A_k^T X B_k^T (B_k B_k^T)^-1 with the r x r solve in
+                            FP64, then the QR of Sec. 3.4.2), 2 = noortho (the ablation of
+                            Sec. 5.4: LQ/QR removed, both Gram inverses, FP64 r x r solves).
+                            1 and 2 run on the generic path (no batches).                 */
 } ttals_config;
 
 /*

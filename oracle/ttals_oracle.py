@@ -41,6 +41,16 @@ Two local-solve modes:
 * ``lsq`` - the exact local least-squares solution for any B_k:
   G~_k = A_k^T X^ B_k^T (B_k B_k^T)^+  (Sec. 3.3, the Gram-matrix form).
 
+and the ablation of Sec. 5.4 ("w/o Ortho", Table ablation_ortho), mode ``noortho``:
+Algorithm 1 with the LQ/QR orthogonalisation steps removed (the normalisation of g_n and
+the LQ sweep of Sec. 3.4.1, the QR and the R propagation of Sec. 3.4.2).  Without
+orthogonal cores the local problem of Eq. proposed-objective-matrix needs the Gram inverses
+that Sec. 3.3 names, so each core is its exact least-squares solution
+G_k = (A_k^T A_k)^+ A_k^T X^ B_k^T (B_k B_k^T)^+ and g_n = (A_n^T A_n)^+ A_n^T vec(X_t)
+(a reading: the paper states only that the steps were removed; with the printed update
+alone the cores would scale without bound, and Table ablation_ortho shows both variants
+equal at t = 10).  In exact arithmetic it spans what ``literal`` spans.
+
 All slices seen so far (Eq. proposed-objective-slice, the per-slice form of Eq.
 proposed-objective-full): ``refit_temporal_rows`` gives the temporal rows that
 minimise it with the cores frozen at their time-t values, and ``global_objective``
@@ -129,7 +139,7 @@ class OnlineTTALS:
     r_1..r_{n-1} (clamped).  ``cores``/``g`` give the initial state (copied)."""
 
     def __init__(self, dims, ranks, cores, g, mode: str = "literal", record: bool = False):
-        if mode not in ("literal", "lsq"):
+        if mode not in ("literal", "lsq", "noortho"):
             raise ValueError(mode)
         self.dims = [int(d) for d in dims]
         self.ranks = clamp_ranks(self.dims, ranks)
@@ -174,15 +184,20 @@ class OnlineTTALS:
         if rec is not None:
             rec["prev_xhat"] = self.reconstruct()
 
+        ortho = self.mode != "noortho"
         # 1. Right orthogonalisation (Sec. 3.4.1)
         rho = float(np.linalg.norm(self.g))
-        if rho > 0.0:
+        if not ortho:
+            if rho == 0.0:                        # zero temporal row: as in the other modes
+                self.g = np.zeros_like(self.g)
+                self.g[0] = 1.0
+        elif rho > 0.0:
             G[m - 1] = rho * G[m - 1]
             self.g = self.g / rho
         else:
             self.g = np.zeros_like(self.g)
             self.g[0] = 1.0
-        for k in range(m - 1, 0, -1):            # cores G_{n-1} .. G_2
+        for k in range(m - 1, 0, -1) if ortho else ():   # cores G_{n-1} .. G_2
             r0, ik, r1 = G[k].shape
             l_mat, q_mat = lq(G[k].reshape(r0, ik * r1))
             G[k] = q_mat.reshape(r0, ik, r1)
@@ -209,25 +224,30 @@ class OnlineTTALS:
             # local solve  G~_k = A_k^T x_2^1 X^_t x_3^1 B_k^T
             t_k = np.tensordot(a_mat.T, xhat3, axes=([1], [0]))            # (r0, ik, rest)
             gt = np.tensordot(t_k, B[k].T, axes=([2], [0]))                # (r0, ik, r1)
-            if self.mode == "lsq":
+            if self.mode in ("lsq", "noortho"):
                 gt = np.tensordot(gt, np.linalg.pinv(B[k] @ B[k].T), axes=([2], [0]))
+            if not ortho:                                                   # (A_k^T A_k)^+
+                gt = np.tensordot(np.linalg.pinv(a_mat.T @ a_mat), gt, axes=([1], [0]))
             if rec is not None:
                 f_old.append(self._local_objective(a_mat, G[k], B[k], xhat3))
                 f_new.append(self._local_objective(a_mat, gt, B[k], xhat3))
                 bbt.append(float(np.linalg.norm(B[k] @ B[k].T - np.eye(r1))))
                 a_list.append(a_mat.copy())
                 gt_list.append(gt.copy())
-            q_mat, r_mat = householder_qr(gt.reshape(r0 * ik, r1))
-            G[k] = q_mat.reshape(r0, ik, r1)
-            if k < m - 1:                                                   # propagate R
-                G[k + 1] = np.tensordot(r_mat, G[k + 1], axes=([1], [0]))
+            if ortho:
+                q_mat, r_mat = householder_qr(gt.reshape(r0 * ik, r1))
+                G[k] = q_mat.reshape(r0, ik, r1)
+                if k < m - 1:                                               # propagate R
+                    G[k + 1] = np.tensordot(r_mat, G[k + 1], axes=([1], [0]))
+                else:
+                    self.g = r_mat @ self.g
             else:
-                self.g = r_mat @ self.g
+                G[k] = gt
             a_mat = (a_mat @ G[k].reshape(r0, ik * r1)).reshape(left * ik, r1)  # A_{k+1}
 
         # 4. Temporal row g_n = A_n^T vec(X_t)
         self.g = a_mat.T @ x.reshape(-1)
-        if self.mode == "lsq":
+        if self.mode in ("lsq", "noortho"):
             self.g = np.linalg.pinv(a_mat.T @ a_mat) @ self.g
         self.t += 1
         xh = (a_mat @ self.g).reshape(dims)

@@ -185,6 +185,7 @@ struct ttals_stream {
   int cfg_env_kernel = 0;             // ttals_config.env_kernel (0: by shape)
   int cfg_k1_split = 0;               // ttals_config.k1_split (0: by shape and batch)
   int cfg_factor = 0;                 // ttals_config.factor (0: FP64 r x r factor, 1: FP32)
+  int mode = 0;                       // ttals_config.mode: 0 literal, 1 lsq, 2 noortho
   size_t bytes = 0;
   std::vector<void*> allocs;
   unsigned long long nlaunch = 0;      // kernels launched by this stream (host counter)
@@ -295,6 +296,12 @@ struct Impl final : ttals_stream {
   double* dout = nullptr;              // FP64 staging for core readout
   bool materialised = false;
   size_t part_elems = 0, y_elems = 0, wpart_elems = 0, sumsq_elems = 0, cc_elems = 0, hh_elems = 0;
+  // Gram-form modes (lsq, noortho): r x r Grams, their FP64 factor, the unweighted environment
+  TC* gM[2] = {};                      // A_k^T A_k of the current and the next level (noortho)
+  TC* gBB = nullptr;                   // B^_k B^_k^T
+  double* gL64 = nullptr;              // FP64 Cholesky factor of the Gram being solved
+  double* gRdiag = nullptr;            // 1 / L_kk
+  TC* gEt = nullptr;                   // A_{k*}^T X_(k*) before the last solve (noortho statistics)
 
   // ---- fused tensor-core path (k* = 2, FP16 / BF16 ingest) -------------------
   static constexpr bool kHalfIngest = std::is_same<TX, __half>::value || std::is_same<TX, __nv_bfloat16>::value;
@@ -386,6 +393,14 @@ struct Impl final : ttals_stream {
     size_t maxcore = 0;
     for (int k = 1; k <= m; ++k) maxcore = std::max<size_t>(maxcore, (size_t)core_elems(k));
     TT_TRY(dalloc(&dout, maxcore));
+    if (mode != 0) {
+      TT_TRY(dalloc(&gM[0], (size_t)kMaxRank * kMaxRank));
+      TT_TRY(dalloc(&gM[1], (size_t)kMaxRank * kMaxRank));
+      TT_TRY(dalloc(&gBB, (size_t)kMaxRank * kMaxRank));
+      TT_TRY(dalloc(&gL64, (size_t)64 * 64));
+      TT_TRY(dalloc(&gRdiag, (size_t)64));
+      TT_TRY(dalloc(&gEt, csz));
+    }
     TT_TRY(dalloc(&ctl, (size_t)nbatch));
     TT_CUDA(cudaMemset(ctl, 0, sizeof(Ctl) * nbatch));
     ctl_base = ctl;
@@ -427,7 +442,7 @@ struct Impl final : ttals_stream {
   // the fused path covers k* = 2 with FP16/BF16 ingest, r_1 <= 64, rows of the slice
   // 16-byte aligned (rest_1 % 8 == 0) and I_1 small enough for one cluster of row chunks
   ttals_status setup_fast() {
-    if (!kHalfIngest || kstar != 2) return TTALS_OK;
+    if (!kHalfIngest || kstar != 2 || mode != 0) return TTALS_OK;
     const long long M = dims[0], J = rest[1];
     const int r = rk(1);
     if (J % 8 != 0 || r > 64 || M > 8 * 512) return TTALS_OK;
@@ -847,7 +862,7 @@ struct Impl final : ttals_stream {
 
   // orthonormal basis of the level-k local solve.  Input: split partials of Y
   // (nsplit x rows x r) in `part`.  Output: Q (rows x r) in `qout`.
-  ttals_status orth(int k, int nsplit, bool first, TC* qout, cudaStream_t s) {
+  ttals_status orth(int k, int nsplit, bool first, TC* qout, cudaStream_t s, const TC* src0 = nullptr) {
     const long long n = rows(k);
     const int r = rk(k);
     const int nb = gram_blocks(n);
@@ -860,10 +875,12 @@ struct Impl final : ttals_stream {
     const int sum_n = (int)sumsq_elems;
     for (int pass = 0; pass < qr_passes; ++pass) {
       const int slot = 2 * (k - 1) + pass;
-      const TC* src = pass == 0 ? (const TC*)part : (const TC*)Qa;
+      // pass 0 reads the split partials of the local solve (or, with src0, the reduced solve
+      // already in Y) and leaves the reduced solve in Y
+      const TC* src = pass == 0 ? (src0 ? src0 : (const TC*)part) : (const TC*)Qa;
       TC* dst = (pass + 1 == qr_passes) ? qout : Qa;
       k_gram<TC, TC, TG><<<nblk, GRAM_THREADS, gsm, s>>>(src, pass == 0 ? nsplit : 1, n * r, n, r,
-                                                          pass == 0 ? Y : nullptr, Wpart, rpb, ctl);
+                                                          (pass == 0 && !src0) ? Y : nullptr, Wpart, rpb, ctl);
       TT_CUDA(cudaGetLastError());
       k_factor<<<1, FACT_THREADS, fsm, s>>>(Wpart, nblk, r, pass == 0 ? 0 : 1, T64, T32, ctl, slot,
                                              sumsq, sum_n, (first && pass == 0) ? 1 : 0);
@@ -888,6 +905,7 @@ struct Impl final : ttals_stream {
   ttals_status push_body(const void* xv, cudaStream_t s) {
     const TX* X = (const TX*)xv;
     if (fast) return push_fast(X, s);
+    if (mode != 0 && kstar > 1) return push_body_gram(X, s);
     const int np = 1 - par;
     materialised = false;
     CopyList rl{};
@@ -957,6 +975,147 @@ struct Impl final : ttals_stream {
       TT_CUDA(cudaGetLastError());
       ++nlaunch;
       if (last_level) ncc = nb;
+    }
+    k_commit<<<1, 256, 0, s>>>(ctl, ccpart, ncc, nullptr, 0, rl);
+    TT_CUDA(cudaGetLastError());
+    ++nlaunch;
+    par = np;
+    return TTALS_OK;
+  }
+
+  // ---- Gram-form modes (Sec. 3.3): the normal equations of each local least-squares problem
+  // S <- S^{-1} applied to n vectors of the matrix V (see k_r64_apply), S an r x r Gram in TC:
+  // the batched FP64 factor kernel (one matrix here) and the FP64 apply
+  ttals_status spd_solve(const TC* S, int r, TC* V, long long n, long long vstride, long long estride,
+                         cudaStream_t s) {
+    const int nb = (int)std::min<long long>(std::max<long long>(1, cdiv(n, 128)), 4 * kSMs);
+    if (r <= 16) {
+      r64::k_r64_factor<TC, 16><<<1, r64::kFactorThreads, 0, s>>>(S, 0, r, 1e-14, gL64, gRdiag, nullptr);
+      r64::k_r64_apply<TC, 16><<<nb, 128, 0, s>>>(gL64, gRdiag, r, V, n, vstride, estride, &ctl->skip);
+    } else if (r <= 32) {
+      r64::k_r64_factor<TC, 32><<<1, r64::kFactorThreads, 0, s>>>(S, 0, r, 1e-14, gL64, gRdiag, nullptr);
+      r64::k_r64_apply<TC, 32><<<nb, 128, 0, s>>>(gL64, gRdiag, r, V, n, vstride, estride, &ctl->skip);
+    } else {
+      r64::k_r64_factor<TC, 64><<<1, r64::kFactorThreads, 0, s>>>(S, 0, r, 1e-14, gL64, gRdiag, nullptr);
+      r64::k_r64_apply<TC, 64><<<nb, 128, 0, s>>>(gL64, gRdiag, r, V, n, vstride, estride, &ctl->skip);
+    }
+    TT_CUDA(cudaGetLastError());
+    nlaunch += 2;
+    return TTALS_OK;
+  }
+
+  // One step of Algorithm 1 with every local solve in its Gram form (mode lsq, with the QR
+  // left-orthogonalisation of Sec. 3.4.2 kept), or with the LQ/QR steps removed as in the
+  // ablation of Sec. 5.4 (mode noortho: G_k = (A_k^T A_k)^-1 A_k^T X B_k^T (B_k B_k^T)^-1, no
+  // orthogonalisation, the collapsed right part C = (A_k*^T A_k*)^-1 A_k*^T X).  In exact
+  // arithmetic both give the reconstruction of the literal update.  Right interfaces as in
+  // push_body (B^_k from the old cores, no LQ sweep).
+  ttals_status push_body_gram(const TX* X, cudaStream_t s) {
+    const int np = 1 - par;
+    const bool ortho = mode == 1;
+    materialised = false;
+    CopyList rl{};
+    for (int k = 1; k < kstar; ++k) {
+      rl.src[rl.n] = G[par][k - 1];
+      rl.dst[rl.n] = G[np][k - 1];
+      rl.bytes[rl.n] = core_elems(k) * (long long)sizeof(TC);
+      ++rl.n;
+    }
+    rl.src[rl.n] = C[par];
+    rl.dst[rl.n] = C[np];
+    rl.bytes[rl.n] = full[kstar - 1] * rest[kstar - 1] * (long long)sizeof(TC);
+    ++rl.n;
+    bool first_launch = true;
+    for (int k = kstar - 2; k >= 1; --k) {
+      const bool fromC = (k == kstar - 2);
+      const TC* Bsrc = fromC ? C[par] : Bhat[k + 1];
+      GemmShape g = plan_gemm(rows(k + 1), (int)rest[k + 1], rk(k + 1), false);
+      TT_TRY((gemm<TC, TC, TC, TC, true, false>(g, G[par][k], rk(k + 1), Bsrc, rest[k + 1], Bhat[k], rest[k + 1],
+                                                 1, 0, nullptr, fromC ? &ctl->cc : nullptr, nullptr,
+                                                 first_launch ? ctl : nullptr, s)));
+      first_launch = false;
+    }
+    int ncc = 0;
+    int mc = 0;                                  // gM[mc] = A_k^T A_k (noortho); A_1 = 1
+    for (int k = 1; k < kstar; ++k) {
+      const bool last_level = (k == kstar - 1);
+      const TC* Bk = last_level ? C[par] : Bhat[k];
+      const double* bz = last_level ? &ctl->cc : nullptr;
+      const int r0 = (int)full[k - 1], r1 = rk(k);
+      const long long n = rows(k);
+      GemmShape gs = plan_solve(k);
+      if (k == 1) {
+        TT_TRY(solve_level1(gs, X, Bk, bz, first_launch ? ctl : nullptr, s));
+        if (!ortho) {                           // (lsq: the first orth pass sums it)
+          k_sum_xx<<<1, 256, 0, s>>>(sumsq, (int)sumsq_elems, ctl);
+          TT_CUDA(cudaGetLastError());
+          ++nlaunch;
+        }
+      } else {
+        TT_TRY((gemm<TC, TC, TC, TC, true, true>(gs, E[k], rest[k], Bk, rest[k], part, r1, 1,
+                                                 (long long)gs.M * gs.N, nullptr, bz, ctl, nullptr, s)));
+      }
+      first_launch = false;
+      // Y = the reduced local solve E_k B^_k^T, (r_{k-1} I_k) x r_k
+      {
+        const int nb = (int)std::min<long long>(cdiv(n * r1, 256), 4 * kSMs);
+        k_reduce_rows<TC><<<nb, 256, 0, s>>>(part, gs.nsplit, n * r1, Y, ctl);
+        TT_CUDA(cudaGetLastError());
+        ++nlaunch;
+      }
+      // Y <- Y (B^_k B^_k^T)^-1 (the right Gram, with the zero-row rule of the literal path)
+      TT_TRY((gemm<TC, TC, TC, TC, true, true>(plan_gemm(r1, r1, rest[k], false), Bk, rest[k], Bk, rest[k], gBB, r1,
+                                               1, 0, nullptr, nullptr, ctl, nullptr, s)));
+      TT_TRY(spd_solve(gBB, r1, Y, n, r1, 1, s));
+      TC* qdst = G[np][k - 1];
+      if (ortho) {
+        TT_TRY(orth(k, 1, k == 1, qdst, s, Y));
+      } else {
+        // G_k = (A_k^T A_k)^-1 acting on the r_{k-1} index of Y: the columns of Y seen as an
+        // r_{k-1} x (I_k r_k) matrix
+        if (k > 1) TT_TRY(spd_solve(gM[mc], r0, Y, (long long)dims[k - 1] * r1, 1, (long long)dims[k - 1] * r1, s));
+        TT_CUDA(cudaMemcpyAsync(qdst, Y, (size_t)(n * r1) * sizeof(TC), cudaMemcpyDeviceToDevice, s));
+      }
+      // environment E_{k+1} = G_k^T E_k (unweighted for noortho)
+      GemmShape ge = plan_env(k);
+      if (k == 1) {
+        TT_TRY(env_level1(ge, X, qdst, s));
+      } else {
+        TT_TRY((gemm<TC, TC, TC, TC, false, false>(ge, E[k], rest[k], qdst, r1, part, r1, 1,
+                                                   (long long)ge.M * ge.N, nullptr, nullptr, ctl, nullptr, s)));
+      }
+      TC* eout = last_level ? C[np] : E[k + 1];
+      const int nbr = (int)std::min<long long>(cdiv(rest[k] * r1, RED_THREADS), 4 * kSMs);
+      k_reduce_t<TC><<<nbr, RED_THREADS, 0, s>>>(part, ge.nsplit, (long long)ge.M * ge.N, rest[k], r1, eout,
+                                                 (last_level && ortho) ? ccpart : nullptr, ctl);
+      TT_CUDA(cudaGetLastError());
+      ++nlaunch;
+      if (last_level && ortho) ncc = nbr;
+      if (!ortho) {
+        // A_{k+1}^T A_{k+1} = G_k^T (A_k^T A_k (x) I) G_k
+        const int mn = 1 - mc;
+        if (k == 1) {
+          TT_TRY((gemm<TC, TC, TC, TC, false, false>(plan_gemm(r1, r1, n, false), qdst, r1, qdst, r1, gM[mn], r1, 1,
+                                                     0, nullptr, nullptr, ctl, nullptr, s)));
+        } else {
+          const long long w = (long long)dims[k - 1] * r1;     // H = M_k G_k (r_{k-1} x I_k r_k) in Qa
+          TT_TRY((gemm<TC, TC, TC, TC, true, false>(plan_gemm(r0, (int)w, r0, false), gM[mc], r0, qdst, w, Qa, w, 1,
+                                                    0, nullptr, nullptr, ctl, nullptr, s)));
+          TT_TRY((gemm<TC, TC, TC, TC, false, false>(plan_gemm(r1, r1, n, false), qdst, r1, Qa, r1, gM[mn], r1, 1, 0,
+                                                     nullptr, nullptr, ctl, nullptr, s)));
+        }
+        mc = mn;
+        if (last_level) {
+          // C = (A_k*^T A_k*)^-1 E~ on the columns of the r_{k*-1} x rest matrix; ||x^||^2 = <E~, C>
+          const long long csz = (long long)r1 * rest[k];
+          TT_CUDA(cudaMemcpyAsync(gEt, eout, (size_t)csz * sizeof(TC), cudaMemcpyDeviceToDevice, s));
+          TT_TRY(spd_solve(gM[mc], r1, eout, rest[k], 1, rest[k], s));
+          ncc = (int)std::min<long long>(cdiv(csz, 256), (long long)kSMs);
+          k_dot_part<TC><<<ncc, 256, 0, s>>>(gEt, eout, csz, ccpart, ctl);
+          TT_CUDA(cudaGetLastError());
+          ++nlaunch;
+        }
+      }
     }
     k_commit<<<1, 256, 0, s>>>(ctl, ccpart, ncc, nullptr, 0, rl);
     TT_CUDA(cudaGetLastError());
@@ -1269,8 +1428,8 @@ static ttals_status create_streams(int nbatch, int n_slice_modes, const int64_t*
   c.device = 0;
   if (cfg) {
     c = *cfg;
-    if (c.reserved[0] != 0) return TTALS_EINVAL;
     if (c.factor != 0 && c.factor != 1) return TTALS_EINVAL;
+    if (c.mode < 0 || c.mode > 2) return TTALS_EINVAL;
     if (c.env_kernel < 0 || c.env_kernel > 4) return TTALS_EINVAL;
     if (c.k1_split != 0 && c.k1_split != 1 && c.k1_split != 2 && c.k1_split != 4 && c.k1_split != 8)
       return TTALS_EINVAL;
@@ -1329,6 +1488,7 @@ static ttals_status create_streams(int nbatch, int n_slice_modes, const int64_t*
   s->cfg_env_kernel = c.env_kernel;
   s->cfg_k1_split = c.k1_split;
   s->cfg_factor = c.factor;
+  s->mode = c.mode;
   if (cudaEventCreateWithFlags(&s->ev, cudaEventDisableTiming) != cudaSuccess) {
     delete s;
     return TTALS_ECUDA;

@@ -338,8 +338,8 @@ __global__ void __launch_bounds__(FACT_THREADS) k_factor(
     for (int i = tid; i < nsum; i += blockDim.x) v += sumsq[i];
     const double xx = block_sum(v, red);
     if (tid == 0) {
-      ctl->xx = xx;
-      if (!isfinite(xx)) { ctl->skip = 1; ctl->latched = 4; }
+      if (!isfinite(xx)) { ctl->skip = 1; ctl->latched = 4; }   // the committed ||x||^2 stays
+      else ctl->xx = xx;
     }
     __syncthreads();
   }
@@ -598,6 +598,45 @@ __global__ void __launch_bounds__(RED_THREADS) k_reduce_t(
     const double tot = block_sum(ss, red);
     if (threadIdx.x == 0) ccpart[blockIdx.x] = tot;
   }
+}
+
+// out = sum of nsplit partial matrices (n elements each, split stride n), in split order
+template <typename TC>
+__global__ void k_reduce_rows(const TC* __restrict__ P, int nsplit, long long n, TC* __restrict__ out,
+                              const Ctl* __restrict__ ctl) {
+  if (ctl && ctl->skip) return;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+    double v = 0.0;
+    for (int q = 0; q < nsplit; ++q) v += Cvt<TC>::d(P[(long long)q * n + e]);
+    out[e] = from_acc<TC>(v);
+  }
+}
+
+// ||x||^2 of the step from the level-1 solve's per-CTA partials (the Gram-form modes, which
+// have no level-1 factor kernel to do it); a non-finite sum marks the step skipped
+// (ENONFINITE latched) and keeps the committed value
+__global__ void k_sum_xx(const double* __restrict__ sumsq, int nsum, Ctl* __restrict__ ctl) {
+  __shared__ double red[32];
+  double v = 0.0;
+  for (int i = threadIdx.x; i < nsum; i += blockDim.x) v += sumsq[i];
+  const double xx = block_sum(v, red);
+  if (threadIdx.x == 0) {
+    if (!isfinite(xx)) { ctl->skip = 1; ctl->latched = 4; }
+    else ctl->xx = xx;
+  }
+}
+
+// per-CTA partials of <a, b> (FP64), written to part[blockIdx.x]
+template <typename TC>
+__global__ void k_dot_part(const TC* __restrict__ a, const TC* __restrict__ b, long long n, double* __restrict__ part,
+                           const Ctl* __restrict__ ctl) {
+  __shared__ double red[32];
+  double ss = 0.0;
+  if (!(ctl && ctl->skip))
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
+      ss += Cvt<TC>::d(a[e]) * Cvt<TC>::d(b[e]);
+  const double tot = block_sum(ss, red);
+  if (threadIdx.x == 0) part[blockIdx.x] = tot;
 }
 
 // --------------------------------------------------------------------------

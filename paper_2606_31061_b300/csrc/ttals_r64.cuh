@@ -165,4 +165,88 @@ __device__ bool ldl_factor(int r, Load load, double tol, Smem& sm, float* LT, in
   return ok;
 }
 
+
+// ---------------------------------------------------------------------------------------
+// The batched FP64 r x r factor kernel (one CTA of four warps per matrix) and the apply of
+// its inverse: the normal-equation solves of the local least-squares problem in its Gram
+// form (Sec. 3.3: the inverses of A_k^T A_k and B_k B_k^T), used by the `lsq` and `noortho`
+// modes of the generic path.
+// ---------------------------------------------------------------------------------------
+constexpr int kFactorThreads = 128;
+
+// Matrix b of the batch: S_b = S + b * s_stride (row-major r x r, symmetric, the lower
+// triangle is read).  Factors D S_b D = L' L'^T in FP64 with D = diag(S_b)^{-1/2} and writes
+// the Cholesky factor of S_b, L = D^{-1} L' (row-major r x r, lower; L_b = L64 + b * 64 * 64)
+// and rdiag_b[k] = 1 / L_kk (rdiag + b * 64).  A pivot of the scaled matrix at or below tol
+// (a direction S_b does not determine) gets rdiag 0 and a zero column: the apply then drops
+// that direction, a generalised inverse in place of S_b^{-1}.  bad[b] (if not null) = 1 when
+// that happened.
+template <typename TS, int RMAX>
+__global__ void __launch_bounds__(kFactorThreads) k_r64_factor(const TS* __restrict__ S, long long s_stride, int r,
+                                                              double tol, double* __restrict__ L64,
+                                                              double* __restrict__ rdiag, int* __restrict__ bad) {
+  __shared__ Smem sm;
+  __shared__ double dsc[kMaxR];
+  const int b = blockIdx.x, tid = threadIdx.x;
+  const TS* Sb = S + (long long)b * s_stride;
+  double* Lb = L64 + (long long)b * kMaxR * kMaxR;
+  for (int e = tid; e < r * r; e += kFactorThreads) Lb[e] = 0.0;
+  if (tid < r) {
+    const double d = (double)Sb[tid * r + tid];
+    dsc[tid] = d > 0.0 ? rsqrt(d) : 0.0;
+  }
+  __syncthreads();
+  const auto load = [&](int i, int j) -> double { return (double)Sb[i * r + j] * dsc[i] * dsc[j]; };
+  const bool ok = ldl_factor<kFactorThreads, RMAX>(r, load, tol, sm, nullptr, 0, nullptr, Lb, r);
+  __syncthreads();
+  // L = D^{-1} L' (rows scaled by sqrt(S_ii)); 1 / L_kk = dsc_k / L'_kk = dsc_k P_k rs_k
+  for (int e = tid; e < r * r; e += kFactorThreads) {
+    const int i = e / r;
+    Lb[e] = dsc[i] > 0.0 ? Lb[e] / dsc[i] : 0.0;
+  }
+  if (tid < r) rdiag[(long long)b * kMaxR + tid] = dsc[tid] * sm.pk[tid] * sm.rs[tid];
+  if (tid == 0 && bad) bad[b] = ok ? 0 : 1;
+}
+
+// v <- S^{-1} v for n vectors of length r (element i of vector t at V[t * vstride + i * estride])
+// with S = L L^T from k_r64_factor: forward then backward substitution in FP64, one thread per
+// vector, L in shared memory.  Returns at once when ctl->skip is set.
+template <typename TV, int RMAX>
+__global__ void __launch_bounds__(128) k_r64_apply(const double* __restrict__ L64, const double* __restrict__ rdiag,
+                                                   int r, TV* __restrict__ V, long long n, long long vstride,
+                                                   long long estride, const int* __restrict__ skip) {
+  if (skip && *skip) return;
+  __shared__ double L[RMAX * RMAX];
+  __shared__ double rd[RMAX];
+  for (int e = threadIdx.x; e < r * r; e += blockDim.x) L[(e / r) * RMAX + e % r] = L64[e];
+  if (threadIdx.x < r) rd[threadIdx.x] = rdiag[threadIdx.x];
+  __syncthreads();
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+    TV* v = V + t * vstride;
+    double y[RMAX];
+#pragma unroll
+    for (int i = 0; i < RMAX; ++i) {
+      if (i < r) {
+        double acc = (double)v[i * estride];
+#pragma unroll
+        for (int k = 0; k < i; ++k) acc = fma(-L[i * RMAX + k], y[k], acc);
+        y[i] = acc * rd[i];
+      } else {
+        y[i] = 0.0;
+      }
+    }
+#pragma unroll
+    for (int i = RMAX - 1; i >= 0; --i) {
+      if (i < r) {
+        double acc = y[i];
+#pragma unroll
+        for (int k = i + 1; k < RMAX; ++k)
+          if (k < r) acc = fma(-L[k * RMAX + i], y[k], acc);
+        y[i] = acc * rd[i];
+        v[i * estride] = (TV)y[i];
+      }
+    }
+  }
+}
+
 }  // namespace r64

@@ -17,6 +17,7 @@ LIB_PATH = os.path.join(_HERE, "libttals.so")
 
 F64, F32, F16, BF16 = 0, 1, 2, 3
 DTYPES = {"f64": F64, "f32": F32, "f16": F16, "bf16": BF16}
+MODES = {"literal": 0, "lsq": 1, "noortho": 2}   # ttals_config.mode
 MAX_BATCH = 64          # TTALS_MAX_BATCH: streams per ttals_create_batch
 STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENONFINITE", 5: "ETIMEOUT", 6: "ESTATE"}
 
@@ -40,7 +41,7 @@ class TTALSError(RuntimeError):
 class Config(ctypes.Structure):
     _fields_ = [("ingest", ctypes.c_int), ("seed", ctypes.c_uint64), ("device", ctypes.c_int),
                 ("qr_passes", ctypes.c_int), ("env_kernel", ctypes.c_int), ("k1_split", ctypes.c_int),
-                ("factor", ctypes.c_int), ("reserved", ctypes.c_int * 1)]
+                ("factor", ctypes.c_int), ("mode", ctypes.c_int)]
 
 
 _lib = None
@@ -117,14 +118,16 @@ class Stream:
 
     def __init__(self, dims: Sequence[int], ranks: Sequence[int], ingest: str = "f64",
                  seed: int = 0x5EED, device: int = 0, qr_passes: int = 0, n_streams: int = 0,
-                 env_kernel: int = 0, k1_split: int = 0, factor: str = "fp64"):
+                 env_kernel: int = 0, k1_split: int = 0, factor: str = "fp64", mode: str = "literal"):
         lib = load()
         self.dims = tuple(int(d) for d in dims)
         self.ingest = ingest
         if factor not in ("fp64", "fp32"):
             raise ValueError(f"factor must be 'fp64' or 'fp32', not {factor!r}")
+        if mode not in MODES:
+            raise ValueError(f"mode must be one of {sorted(MODES)}, not {mode!r}")
         cfg = Config(DTYPES[ingest], seed, device, qr_passes, env_kernel, k1_split, 0 if factor == "fp64" else 1,
-                     (ctypes.c_int * 1)(0))
+                     MODES[mode])
         h = ctypes.c_void_p()
         if n_streams > 0:
             code = lib.ttals_create_batch(int(n_streams), len(self.dims), _i64(self.dims), _i64(ranks),

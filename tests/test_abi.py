@@ -44,16 +44,16 @@ def test_invalid_arguments_rejected_before_cuda(lib):
     assert lib.ttals_create(2, dims, ranks, None, ctypes.byref(h)) == 1      # EINVAL: I_2 = 0
     dims = (ctypes.c_int64 * 1)(4)
     assert lib.ttals_create(1, dims, ranks, None, ctypes.byref(h)) == 1      # one slice mode
-    cfg = T.Config(7, 1, 0, 0, 0, 0, 0, (ctypes.c_int * 1)(0))
+    cfg = T.Config(7, 1, 0, 0, 0, 0, 0, 0)
     dims = (ctypes.c_int64 * 2)(4, 4)
     assert lib.ttals_create(2, dims, ranks, ctypes.byref(cfg), ctypes.byref(h)) == 1   # bad dtype
-    cfg = T.Config(0, 1, 0, 0, 0, 0, 0, (ctypes.c_int * 1)(1))
-    assert lib.ttals_create(2, dims, ranks, ctypes.byref(cfg), ctypes.byref(h)) == 1   # reserved != 0
-    cfg = T.Config(2, 1, 0, 0, 0, 0, 2, (ctypes.c_int * 1)(0))
+    cfg = T.Config(0, 1, 0, 0, 0, 0, 0, 3)
+    assert lib.ttals_create(2, dims, ranks, ctypes.byref(cfg), ctypes.byref(h)) == 1   # mode 3
+    cfg = T.Config(2, 1, 0, 0, 0, 0, 2, 0)
     assert lib.ttals_create(2, dims, ranks, ctypes.byref(cfg), ctypes.byref(h)) == 1   # factor 2
-    cfg = T.Config(2, 1, 0, 0, 5, 0, 0, (ctypes.c_int * 1)(0))
+    cfg = T.Config(2, 1, 0, 0, 5, 0, 0, 0)
     assert lib.ttals_create(2, dims, ranks, ctypes.byref(cfg), ctypes.byref(h)) == 1   # env_kernel 5
-    cfg = T.Config(2, 1, 0, 0, 0, 3, 0, (ctypes.c_int * 1)(0))
+    cfg = T.Config(2, 1, 0, 0, 0, 3, 0, 0)
     assert lib.ttals_create(2, dims, ranks, ctypes.byref(cfg), ctypes.byref(h)) == 1   # k1_split 3
     ranks = (ctypes.c_int64 * 2)(65, 65)
     dims = (ctypes.c_int64 * 2)(100, 100)
