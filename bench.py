@@ -179,8 +179,8 @@ def time_arm(ingest, steps, warmup, pool, dist_on, sampler_idx, factor="fp64", d
     # host cost of one push: a short burst enqueued while the device is busy (the launch
     # queue does not fill, so no back-pressure is included)
     torch.cuda._sleep(int(2e8))
-    nb = min(64, warmup)
-    burst = [ptrs[pingpong(t, P)] for t in range(nb)]   # slices seen in the warm-up (maps cached)
+    nb = 64
+    burst = [ptrs[pingpong(t % warmup, P)] for t in range(nb)]   # slices seen in the warm-up (maps cached)
     h0 = time.perf_counter()
     for p in burst:
         st.push_ptr(p, h)
@@ -413,8 +413,14 @@ def serve_arm(seconds=2.0, n=256, lam=30.0, budget=150e9, slots=8, rank_step=16,
         events += [(float(tt), sid) for tt in t if tt <= seconds]
     events.sort()
 
-    def run(evts, realtime):
-        srv = serve.Server(int(budget), slots=slots, rank_step=rank_step, wire="u8")
+    from oracle import ttals_oracle as O
+    from paper_2606_31061_b300 import synth
+    init = lambda sid, d, r: synth.init_cores(d, r, seed=20000 + sid)
+    sample = [next(sid for sid in range(n) if specs[sid][0] == d) for d in SERVE_SIZES]
+    checked = {}
+
+    def run(evts, realtime, check=False):
+        srv = serve.Server(int(budget), slots=slots, rank_step=rank_step, wire="u8", init_cores=init)
         admitted = sum(srv.connect(sid, d, r) for sid, (d, r) in enumerate(specs))
         torch.cuda.synchronize()
         nxt = {sid: 0 for sid in range(n)}
@@ -439,6 +445,19 @@ def serve_arm(seconds=2.0, n=256, lam=30.0, budget=150e9, slots=8, rank_step=16,
             srv.tick()
             srv.poll()
         t1 = time.perf_counter()
+        if check:
+            # sampled served streams (one per frame size) against the oracle on the frames they got
+            for sid in sample:
+                pool, slot = srv.where[sid]
+                pool.batch.select(slot)
+                s_ = pool.batch.stats()
+                d, rr = specs[sid][0], tuple(pool.batch.ranks)
+                fr = [frames[d][i % len(frames[d])].numpy().astype(np.float64) for i in range(pool.batch.step())]
+                orc = O.OnlineTTALS(d, list(rr), *init(sid, d, rr))
+                re_o = O.stream_relative_error(fr, [orc.step(x) for x in fr])
+                re_g = math.sqrt(s_[3] / s_[2]) if s_[2] > 0 else float("nan")
+                checked["x".join(map(str, d))] = {"ranks": rr, "frames": len(fr), "re_gpu": re_g,
+                                                  "re_oracle": re_o, "abs_diff_re": abs(re_g - re_o)}
         out = {"frames": len(srv.latencies), "seconds": t1 - t0, "steps": srv.steps, "admitted": admitted,
                "pools": sum(len(v) for v in srv.pools.values()), "device_gb": srv.used / 1e9,
                "h2d_gbs": h2d / (t1 - t0) / 1e9, "latency_s": serve.percentiles(srv.latencies)}
@@ -446,28 +465,37 @@ def serve_arm(seconds=2.0, n=256, lam=30.0, budget=150e9, slots=8, rank_step=16,
         torch.cuda.empty_cache()
         return out
 
-    rt = run(events, True)
+    rt = run(events, True, check=True)
     half = [e for j, e in enumerate(events) if j % 2 == 0]     # every other arrival: lam / 2
     rt_half = run(half, True)
     cap_events = [(0.0, sid) for sid in range(n) for _ in range(4)]
     cap = run(cap_events, False)
-    # per-stream FP64 path: one stream per size, device-resident FP64 frames, device-timed
+    # per-stream FP64 path, one stream per size at the ranks its sampled served stream got, the
+    # same 8-bit frames over the host link widened on the device (to FP64), wall time per frame
+    from paper_2606_31061_b300.ttals import widen_u8
     fp64 = {}
     for dims in SERVE_SIZES:
-        st = Stream(dims, (32,) * len(dims), ingest="f64")
-        x = frames[dims][0].cuda().double()         # the same pixels, FP64 ingest
-        for _ in range(2):
+        rr = checked.get("x".join(map(str, dims)), {}).get("ranks") or serve.feasible_ranks(dims, (32,) * len(dims))
+        st = Stream(dims, rr, ingest="f64")
+        stage = torch.empty(dims, dtype=torch.uint8, device="cuda")
+        x = torch.empty(dims, dtype=torch.float64, device="cuda")
+        hf = frames[dims]
+
+        def one(i):
+            stage.copy_(hf[i % len(hf)], non_blocking=True)
+            widen_u8(stage, x)
             st.push(x)
+
+        for i in range(2):
+            one(i)
         torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        for _ in range(5):
-            st.push(x)
-        e1.record()
+        t0 = time.perf_counter()
+        for i in range(6):
+            one(i)
         torch.cuda.synchronize()
-        fp64["x".join(map(str, dims))] = 5 / (e0.elapsed_time(e1) / 1000.0)
+        fp64["x".join(map(str, dims))] = 6 / (time.perf_counter() - t0)
         st.close()
-        del x
+        del x, stage
     fp64_mix = 1.0 / sum((1.0 / 3) / v for v in fp64.values())
     lat = rt["latency_s"]
     return {
@@ -485,6 +513,7 @@ def serve_arm(seconds=2.0, n=256, lam=30.0, budget=150e9, slots=8, rank_step=16,
                       "latency_ms": {"p50": rt_half["latency_s"]["p50"] * 1e3, "p99": rt_half["latency_s"]["p99"] * 1e3,
                                      "n": rt_half["latency_s"]["n"]}, "run": rt_half},
         "capacity_slices_s": cap["frames"] / cap["seconds"], "capacity_run": cap,
+        "served_vs_oracle": checked,
         "fp64_plain_per_stream_slices_s": fp64, "fp64_plain_mix_capacity_slices_s": fp64_mix,
         "vs_fp64_plain_capacity": (cap["frames"] / cap["seconds"]) / fp64_mix,
     }

@@ -283,7 +283,7 @@ int ttals_batch_size(const ttals_stream *s);
 
 /*
  * ttals_widen_u8 - enqueue on cuda_stream dst[i] = src[i] for n 8-bit unsigned values,
- *   widened to dst_dtype (F16, BF16 or F32; exact, since 0..255 are representable).
+ *   widened to dst_dtype (F16, BF16, F32 or F64; exact, since 0..255 are representable).
  *   The paper's video slices are 8-bit pixels (Sec. 5.1): a serving loop that receives
  *   them from the host can move bytes over the host link and widen on the device, half
  *   the traffic of FP16.  src and dst: device memory, 16-byte aligned, owned by the

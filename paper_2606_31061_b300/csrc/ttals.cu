@@ -1719,7 +1719,8 @@ ttals_status ttals_profile_read(ttals_stream* s, double ms_out[4], int64_t* n_ou
 ttals_status ttals_widen_u8(const void* src_dev, void* dst_dev, ttals_dtype dst_dtype, int64_t n,
                             void* cuda_stream) {
   if (!src_dev || !dst_dev || n < 0) return TTALS_EINVAL;
-  if (dst_dtype != TTALS_F16 && dst_dtype != TTALS_BF16 && dst_dtype != TTALS_F32) return TTALS_EINVAL;
+  if (dst_dtype != TTALS_F16 && dst_dtype != TTALS_BF16 && dst_dtype != TTALS_F32 && dst_dtype != TTALS_F64)
+    return TTALS_EINVAL;
   if (((uintptr_t)src_dev & 15u) != 0 || ((uintptr_t)dst_dev & 15u) != 0) return TTALS_EINVAL;
   if (n == 0) return TTALS_OK;
   cudaStream_t st = (cudaStream_t)cuda_stream;
@@ -1734,7 +1735,8 @@ ttals_status ttals_widen_u8(const void* src_dev, void* dst_dev, ttals_dtype dst_
     case TTALS_BF16:
       k_widen_u8<__nv_bfloat16><<<nb, 256, 0, st>>>((const uint8_t*)src_dev, (__nv_bfloat16*)dst_dev, n);
       break;
-    default: k_widen_u8<float><<<nb, 256, 0, st>>>((const uint8_t*)src_dev, (float*)dst_dev, n); break;
+    case TTALS_F32: k_widen_u8<float><<<nb, 256, 0, st>>>((const uint8_t*)src_dev, (float*)dst_dev, n); break;
+    default: k_widen_u8<double><<<nb, 256, 0, st>>>((const uint8_t*)src_dev, (double*)dst_dev, n); break;
   }
   TT_CUDA(cudaGetLastError());
   return TTALS_OK;

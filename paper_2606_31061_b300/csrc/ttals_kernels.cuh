@@ -752,15 +752,10 @@ __global__ void __launch_bounds__(256) k_widen_u8(const uint8_t* __restrict__ sr
     TD o[16];
 #pragma unroll
     for (int q = 0; q < 16; ++q) o[q] = from_acc<TD>((float)((w[q >> 2] >> (8 * (q & 3))) & 0xffu));
-    if constexpr (sizeof(TD) == 2) {
-      uint4* d = reinterpret_cast<uint4*>(dst + c * 16);
-      d[0] = *reinterpret_cast<const uint4*>(&o[0]);
-      d[1] = *reinterpret_cast<const uint4*>(&o[8]);
-    } else {
-      uint4* d = reinterpret_cast<uint4*>(dst + c * 16);
+    constexpr int NQ = (int)sizeof(TD);            // 16-byte chunks of 16 outputs
+    uint4* d = reinterpret_cast<uint4*>(dst + c * 16);
 #pragma unroll
-      for (int q = 0; q < 4; ++q) d[q] = *reinterpret_cast<const uint4*>(&o[4 * q]);
-    }
+    for (int q = 0; q < NQ; ++q) d[q] = reinterpret_cast<const uint4*>(o)[q];
   }
   if (blockIdx.x == 0 && threadIdx.x == 0)
     for (long long e = n16 * 16; e < n; ++e) dst[e] = from_acc<TD>((float)src[e]);

@@ -273,7 +273,7 @@ class Stream:
 
 
 def widen_u8(src, dst, stream=None):
-    """ttals_widen_u8: dst (CUDA float16/bfloat16/float32) = src (CUDA uint8), exact."""
+    """ttals_widen_u8: dst (CUDA float16/bfloat16/float32/float64) = src (CUDA uint8), exact."""
     dt = DTYPES[_TORCH_DTYPES[str(dst.dtype).replace("torch.", "")]]
     _check(load().ttals_widen_u8(ctypes.c_void_p(src.data_ptr()), ctypes.c_void_p(dst.data_ptr()), dt,
                                  ctypes.c_int64(src.numel()), ctypes.c_void_p(_stream_handle(stream))),
