@@ -178,14 +178,16 @@ def time_arm(ingest, steps, warmup, pool, dist_on, sampler_idx, factor="fp64", d
     order = [ptrs[pingpong(warmup + t, P)] for t in range(steps)]
     # host cost of one push: a short burst enqueued while the device is busy (the launch
     # queue does not fill, so no back-pressure is included)
-    torch.cuda._sleep(int(2e8))
-    nb = 64
+    nb = 200
     burst = [ptrs[pingpong(t % warmup, P)] for t in range(nb)]   # slices seen in the warm-up (maps cached)
-    h0 = time.perf_counter()
-    for p in burst:
-        st.push_ptr(p, h)
-    host_us = (time.perf_counter() - h0) / nb * 1e6
-    torch.cuda.synchronize()
+    host_us = float("inf")
+    for _ in range(3):                                           # best of three bursts
+        torch.cuda._sleep(int(1e9))
+        h0 = time.perf_counter()
+        for p in burst:
+            st.push_ptr(p, h)
+        host_us = min(host_us, (time.perf_counter() - h0) / nb * 1e6)
+        torch.cuda.synchronize()
     n0 = st.launch_count
     w0 = time.time()
     e0.record(stream)
@@ -392,7 +394,8 @@ def _serve_frames(nframes=6):
     return pools
 
 
-def serve_arm(seconds=2.0, n=256, lam=30.0, budget=150e9, slots=8, rank_step=16, quantum=0.002):
+def serve_arm(seconds=2.0, n=256, lam=30.0, budget=150e9, slots=8, rank_step=16, quantum=0.002, check=True,
+              fp64_compare=True):
     """Continuous-batching serving loop (paper_2606_31061_b300.serve) in real time: n streams,
     Poisson frame arrivals at `lam` frames/s each for `seconds`, admission by an HBM budget.
     Latency per frame = detection of its step's completion - arrival.  Ranks are rounded up
@@ -422,6 +425,15 @@ def serve_arm(seconds=2.0, n=256, lam=30.0, budget=150e9, slots=8, rank_step=16,
     def run(evts, realtime, check=False):
         srv = serve.Server(int(budget), slots=slots, rank_step=rank_step, wire="u8", init_cores=init)
         admitted = sum(srv.connect(sid, d, r) for sid, (d, r) in enumerate(specs))
+        # warm the pools (their first steps pay one-time costs), then restart every stream
+        for sid, (d, r) in enumerate(specs):
+            if srv.admitted(sid):
+                srv.submit(sid, frames[d][0], 0.0)
+        while srv.backlog():
+            srv.tick()
+            torch.cuda.synchronize()
+            srv.poll()
+        srv.restart_streams()
         torch.cuda.synchronize()
         nxt = {sid: 0 for sid in range(n)}
         h2d = 0
@@ -465,7 +477,7 @@ def serve_arm(seconds=2.0, n=256, lam=30.0, budget=150e9, slots=8, rank_step=16,
         torch.cuda.empty_cache()
         return out
 
-    rt = run(events, True, check=True)
+    rt = run(events, True, check=check)
     half = [e for j, e in enumerate(events) if j % 2 == 0]     # every other arrival: lam / 2
     rt_half = run(half, True)
     cap_events = [(0.0, sid) for sid in range(n) for _ in range(4)]
@@ -474,7 +486,7 @@ def serve_arm(seconds=2.0, n=256, lam=30.0, budget=150e9, slots=8, rank_step=16,
     # same 8-bit frames over the host link widened on the device (to FP64), wall time per frame
     from paper_2606_31061_b300.ttals import widen_u8
     fp64 = {}
-    for dims in SERVE_SIZES:
+    for dims in (SERVE_SIZES if fp64_compare else ()):
         rr = checked.get("x".join(map(str, dims)), {}).get("ranks") or serve.feasible_ranks(dims, (32,) * len(dims))
         st = Stream(dims, rr, ingest="f64")
         stage = torch.empty(dims, dtype=torch.uint8, device="cuda")
@@ -496,7 +508,7 @@ def serve_arm(seconds=2.0, n=256, lam=30.0, budget=150e9, slots=8, rank_step=16,
         fp64["x".join(map(str, dims))] = 6 / (time.perf_counter() - t0)
         st.close()
         del x, stage
-    fp64_mix = 1.0 / sum((1.0 / 3) / v for v in fp64.values())
+    fp64_mix = 1.0 / sum((1.0 / 3) / v for v in fp64.values()) if fp64 else None
     lat = rt["latency_s"]
     return {
         "workload": f"{n} streams, sizes in thirds 256x256 / 720x1280x3 / 1080x1920x3, ranks U[8,48] per bond "
@@ -515,7 +527,7 @@ def serve_arm(seconds=2.0, n=256, lam=30.0, budget=150e9, slots=8, rank_step=16,
         "capacity_slices_s": cap["frames"] / cap["seconds"], "capacity_run": cap,
         "served_vs_oracle": checked,
         "fp64_plain_per_stream_slices_s": fp64, "fp64_plain_mix_capacity_slices_s": fp64_mix,
-        "vs_fp64_plain_capacity": (cap["frames"] / cap["seconds"]) / fp64_mix,
+        "vs_fp64_plain_capacity": (cap["frames"] / cap["seconds"]) / fp64_mix if fp64_mix else None,
     }
 
 

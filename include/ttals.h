@@ -282,6 +282,31 @@ ttals_status ttals_batch_select(ttals_stream *s, int index);
 int ttals_batch_size(const ttals_stream *s);
 
 /*
+ * Host ingest of a batch, for serving loops (one call per step instead of one copy per frame
+ * from the caller; the paper has no counterpart: it streams one slice at a time).
+ * ttals_batch_ingest_init - give the batch its own double-buffered input blocks
+ *   ([n_streams][slice] in the ingest type; with u8_wire = 1 also 8-bit staging, the frames
+ *   then being 8-bit pixels widened on the device, exact), a high-priority copy stream, a
+ *   compute stream and a ring of 256 completion events.  Allocates (counted by
+ *   ttals_device_bytes); call once, before serving.  Ingest F16, BF16 or F32.
+ *   Errors: EINVAL, ESTATE (already initialised), ENOMEM, ECUDA.
+ * ttals_batch_push_host - one masked step of the batch: n frames (1 <= n <= n_streams), frame
+ *   i for stream slots[i] (distinct) from host_frames[i] (pinned host memory, the slice in the
+ *   ingest type, or bytes with the 8-bit wire; the caller keeps it unchanged until the step's
+ *   ticket is done).  Enqueues the copies, the widening, the step of the streams given a frame
+ *   (the others keep their state, as in ttals_push_batch_masked) and a completion event, and
+ *   returns its ticket (0, 1, 2, ...).  Errors (nothing enqueued): EINVAL, ECUDA.
+ * ttals_batch_ticket_done - *done = 1 once the step of `ticket` has completed on the device,
+ *   else 0 (no synchronisation).  Only the 256 most recent tickets are tracked: an older
+ *   ticket reports the completion of a later step (never earlier than its own).
+ *   Errors: EINVAL (unknown ticket), ECUDA.
+ */
+ttals_status ttals_batch_ingest_init(ttals_stream *s, int u8_wire);
+ttals_status ttals_batch_push_host(ttals_stream *s, int n, const int *slots, const void *const *host_frames,
+                                   uint64_t *ticket_out);
+ttals_status ttals_batch_ticket_done(ttals_stream *s, uint64_t ticket, int *done);
+
+/*
  * ttals_widen_u8 - enqueue on cuda_stream dst[i] = src[i] for n 8-bit unsigned values,
  *   widened to dst_dtype (F16, BF16, F32 or F64; exact, since 0..255 are representable).
  *   The paper's video slices are 8-bit pixels (Sec. 5.1): a serving loop that receives

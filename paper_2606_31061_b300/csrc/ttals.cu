@@ -200,11 +200,36 @@ struct ttals_stream {
   size_t ev_used = 0;
   static constexpr int kProfEvents = 6; // push begin, solve1 begin, solve1 end, env1 begin, env1 end, push end
 
+  // host ingest of a batch (ttals_batch_ingest_init / ttals_batch_push_host): the batch owns
+  // double-buffered input blocks, 8-bit staging, a copy and a compute stream and a ring of
+  // completion events, so that one call per step moves the frames and steps the batch
+  struct HostIngest {
+    bool on = false;
+    bool u8 = false;
+    void* block[2] = {};              // [nbatch][slice] in the ingest type
+    void* stage[2] = {};              // [nbatch][slice] bytes (8-bit wire)
+    cudaStream_t copy = nullptr, comp = nullptr;
+    cudaEvent_t copied[2] = {}, consumed[2] = {};
+    std::vector<cudaEvent_t> done;    // ring of completion events, one per ticket
+    uint64_t ticket = 0;
+    int flip = 0;
+  } hi;
+  static constexpr int kTicketRing = 256;
+
   virtual ~ttals_stream() {
     if (have_last) cudaStreamSynchronize(last);
+    if (hi.copy) cudaStreamSynchronize(hi.copy);
+    if (hi.comp) cudaStreamSynchronize(hi.comp);
     for (void* p : allocs) cudaFree(p);
     for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);
     if (ev) cudaEventDestroy(ev);
+    for (int i = 0; i < 2; ++i) {
+      if (hi.copied[i]) cudaEventDestroy(hi.copied[i]);
+      if (hi.consumed[i]) cudaEventDestroy(hi.consumed[i]);
+    }
+    for (cudaEvent_t e : hi.done) cudaEventDestroy(e);
+    if (hi.copy) cudaStreamDestroy(hi.copy);
+    if (hi.comp) cudaStreamDestroy(hi.comp);
   }
   // event slot `i` of the current push (profiling only)
   ttals_status mark(int i, cudaStream_t s) {
@@ -226,6 +251,8 @@ struct ttals_stream {
   // batches: only the fused path steps several streams per launch
   virtual bool batch_capable() const { return false; }
   virtual ttals_status select_slot(int idx) { return idx == 0 ? TTALS_OK : TTALS_EINVAL; }
+  // encode (and cache) the fused path's TMA maps of a slice buffer ahead of its first push
+  virtual ttals_status warm_slice(const void* x) { (void)x; return TTALS_OK; }
 
   long long slice_elems() const { return rest[0]; }
   long long core_elems(int k) const {   // k = 1..m
@@ -612,6 +639,15 @@ struct Impl final : ttals_stream {
         !encode_map_3d(&sm.m[2], X, bf, nbatch, dims[0], rest[1], fast::K1T_BM))
       return nullptr;
     return map_cache.emplace((const void*)X, sm).first->second.m;
+  }
+
+  ttals_status warm_slice(const void* x) override {
+    if (!fast) return TTALS_OK;
+    if (!slice_maps((const TX*)x)) {
+      g_last_err = "cuTensorMapEncodeTiled failed";
+      return TTALS_ECUDA;
+    }
+    return TTALS_OK;
   }
 
   template <int NP>
@@ -1555,6 +1591,103 @@ ttals_status ttals_push_batch_masked(ttals_stream* s, const void* slices_dev, tt
   const ttals_status r = s->push(slices_dev, st);
   s->active_mask = ~0ull;
   return r;
+}
+
+ttals_status ttals_batch_ingest_init(ttals_stream* s, int u8_wire) {
+  if (!s || (u8_wire != 0 && u8_wire != 1)) return TTALS_EINVAL;
+  if (s->ingest != TTALS_F16 && s->ingest != TTALS_BF16 && s->ingest != TTALS_F32) return TTALS_EINVAL;
+  if (s->hi.on) return TTALS_ESTATE;
+  TT_TRY(set_device(s->device));
+  auto& h = s->hi;
+  const size_t n = (size_t)s->nbatch * (size_t)s->slice_elems();
+  for (int p = 0; p < 2; ++p) {
+    if (s->ingest == TTALS_F32) {
+      float* b = nullptr;
+      TT_TRY(s->dalloc(&b, n));
+      h.block[p] = b;
+    } else {
+      __half* b = nullptr;
+      TT_TRY(s->dalloc(&b, n));
+      h.block[p] = b;
+    }
+    if (u8_wire) {
+      uint8_t* st = nullptr;
+      TT_TRY(s->dalloc(&st, n + 16));
+      h.stage[p] = st;
+    }
+  }
+  int lo = 0, hiprio = 0;
+  TT_CUDA(cudaDeviceGetStreamPriorityRange(&lo, &hiprio));
+  // copies (and the widening) at high priority: queued behind other batches' compute they
+  // would leave the host link idle
+  TT_CUDA(cudaStreamCreateWithPriority(&h.copy, cudaStreamNonBlocking, hiprio));
+  TT_CUDA(cudaStreamCreateWithPriority(&h.comp, cudaStreamNonBlocking, lo));
+  for (int p = 0; p < 2; ++p) {
+    TT_CUDA(cudaEventCreateWithFlags(&h.copied[p], cudaEventDisableTiming));
+    TT_CUDA(cudaEventCreateWithFlags(&h.consumed[p], cudaEventDisableTiming));
+    TT_CUDA(cudaEventRecord(h.consumed[p], h.comp));
+  }
+  h.done.resize(ttals_stream::kTicketRing, nullptr);
+  for (auto& e : h.done) TT_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  h.u8 = u8_wire != 0;
+  // the blocks' TMA maps now, not in the first served steps
+  for (int p = 0; p < 2; ++p) TT_TRY(s->warm_slice(h.block[p]));
+  h.on = true;
+  return TTALS_OK;
+}
+
+ttals_status ttals_batch_push_host(ttals_stream* s, int n, const int* slots, const void* const* host_frames,
+                                   uint64_t* ticket_out) {
+  if (!s || !s->hi.on || n < 0 || n > s->nbatch || (n > 0 && (!slots || !host_frames)) || !ticket_out)
+    return TTALS_EINVAL;
+  unsigned long long mask = 0;
+  for (int i = 0; i < n; ++i) {
+    if (slots[i] < 0 || slots[i] >= s->nbatch || !host_frames[i]) return TTALS_EINVAL;
+    if ((mask >> slots[i]) & 1ull) return TTALS_EINVAL;      // one frame per stream and step
+    mask |= 1ull << slots[i];
+  }
+  if (n == 0) return TTALS_EINVAL;
+  TT_TRY(set_device(s->device));
+  auto& h = s->hi;
+  const int p = h.flip;
+  const size_t elems = (size_t)s->slice_elems();
+  const size_t esz = dtype_size(s->ingest);
+  TT_CUDA(cudaStreamWaitEvent(h.copy, h.consumed[p], 0));   // the block's previous step is done with it
+  for (int i = 0; i < n; ++i) {
+    if (h.u8) {
+      TT_CUDA(cudaMemcpyAsync((uint8_t*)h.stage[p] + (size_t)slots[i] * elems, host_frames[i], elems,
+                              cudaMemcpyHostToDevice, h.copy));
+    } else {
+      TT_CUDA(cudaMemcpyAsync((unsigned char*)h.block[p] + (size_t)slots[i] * elems * esz, host_frames[i],
+                              elems * esz, cudaMemcpyHostToDevice, h.copy));
+    }
+  }
+  if (h.u8) {
+    // one widening launch for the block (slots without a frame are widened too and not read)
+    TT_TRY(ttals_widen_u8(h.stage[p], h.block[p], s->ingest, (int64_t)((size_t)s->nbatch * elems), h.copy));
+  }
+  TT_CUDA(cudaEventRecord(h.copied[p], h.copy));
+  TT_CUDA(cudaStreamWaitEvent(h.comp, h.copied[p], 0));
+  TT_TRY(ttals_push_batch_masked(s, h.block[p], s->ingest, mask, h.comp));
+  TT_CUDA(cudaEventRecord(h.consumed[p], h.comp));
+  TT_CUDA(cudaEventRecord(h.done[h.ticket % ttals_stream::kTicketRing], h.comp));
+  *ticket_out = h.ticket++;
+  h.flip ^= 1;
+  return TTALS_OK;
+}
+
+ttals_status ttals_batch_ticket_done(ttals_stream* s, uint64_t ticket, int* done) {
+  if (!s || !s->hi.on || !done || ticket >= s->hi.ticket) return TTALS_EINVAL;
+  const cudaError_t e = cudaEventQuery(s->hi.done[ticket % ttals_stream::kTicketRing]);
+  if (e == cudaSuccess) {
+    *done = 1;
+  } else if (e == cudaErrorNotReady) {
+    *done = 0;
+  } else {
+    g_last_err = std::string("cudaEventQuery: ") + cudaGetErrorString(e);
+    return TTALS_ECUDA;
+  }
+  return TTALS_OK;
 }
 
 ttals_status ttals_batch_select(ttals_stream* s, int index) {

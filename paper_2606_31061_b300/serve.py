@@ -12,9 +12,9 @@ with continuous batching:
   so that streams with nearby ranks share pools; the stream then tracks with the rounded
   ranks (at least the accuracy it asked for).
 * **Steps.** ``tick()`` takes, for every pool, the oldest pending frame of each of its
-  streams, copies them host -> device into the pool's next input block on a copy stream,
-  and enqueues one masked batch step (``ttals_push_batch_masked``: only the streams with a
-  frame step) on the pool's compute stream.  Pools have their own CUDA streams, so the
+  streams and hands them to the library in one call (``ttals_batch_push_host``): it copies
+  them host -> device into the pool's next input block on the pool's copy stream and
+  enqueues one masked batch step (only the streams with a frame step) on its compute stream.  Pools have their own CUDA streams, so the
   work of different pools overlaps on the GPU; frames that arrive while a step is in
   flight wait for the pool's next tick.
 * **Wire format.** With ``wire="u8"`` frames are 8-bit pixels (the paper's video data):
@@ -55,30 +55,16 @@ def feasible_ranks(dims: Sequence[int], ranks: Sequence[int]) -> Tuple[int, ...]
 
 
 class _Pool:
-    """Device side of a pool: batch, input blocks, CUDA streams and events."""
+    """Device side of a pool: a batch with the library's host ingest (its own double-buffered
+    input blocks, 8-bit staging, copy and compute streams, completion tickets)."""
 
     def __init__(self, dims, ranks, slots, ingest, wire="f16"):
-        import torch
         from .ttals import Stream
         self.dims, self.ranks, self.slots = tuple(dims), tuple(ranks), int(slots)
         self.batch = Stream(dims, ranks, ingest=ingest, n_streams=self.slots)
-        dt = torch.float16 if ingest == "f16" else torch.bfloat16
-        self.inputs = torch.zeros((2, self.slots) + self.dims, dtype=dt, device="cuda")
         self.wire = wire
-        self.stage = (torch.zeros((2, self.slots) + self.dims, dtype=torch.uint8, device="cuda")
-                      if wire == "u8" else None)
-        # copies (and the widening of 8-bit frames) run at high priority: a widening kernel
-        # queued behind other pools' compute would hold the host link idle
-        self.copy = torch.cuda.Stream(priority=-5)
-        self.comp = torch.cuda.Stream()
-        self.copied = [torch.cuda.Event() for _ in range(2)]
-        self.consumed = [torch.cuda.Event() for _ in range(2)]
-        for e in self.consumed:
-            e.record(self.comp)
-        self.flip = 0
-        self.bytes = self.batch.device_bytes + self.inputs.numel() * self.inputs.element_size()
-        if self.stage is not None:
-            self.bytes += self.stage.numel()
+        self.batch.ingest_init(u8=(wire == "u8"))
+        self.bytes = self.batch.device_bytes
 
     def reset_slot(self, slot, sid, init_cores=None):
         """A new stream in this slot: its initial cores (the library's default random cores
@@ -94,36 +80,28 @@ class _Pool:
             self.batch.seed_cores((zlib.crc32(repr(sid).encode()) & 0x7FFFFFFF) + 1)
 
     def step(self, frames: Dict[int, object]):
-        """frames: slot -> pinned host tensor.  Returns the step's completion event."""
-        import torch
-        p = self.flip
-        self.flip ^= 1
-        blk = self.inputs[p]
-        with torch.cuda.stream(self.copy):
-            self.copy.wait_event(self.consumed[p])
-            for slot, f in frames.items():
-                if self.stage is None:
-                    blk[slot].copy_(f, non_blocking=True)
-                else:
-                    self.stage[p, slot].copy_(f, non_blocking=True)
-            if self.stage is not None:
-                # one widening launch for the whole block (slots without a frame this step
-                # are widened too and never read: the masked step skips them)
-                from .ttals import widen_u8
-                widen_u8(self.stage[p], blk, stream=self.copy)
-            self.copied[p].record(self.copy)
-        self.comp.wait_event(self.copied[p])
-        mask = 0
-        for slot in frames:
-            mask |= 1 << slot
-        self.batch.push_batch_ptr(blk.data_ptr(), self.comp.cuda_stream, mask)
-        self.consumed[p].record(self.comp)
-        done = torch.cuda.Event()
-        done.record(self.comp)
-        return done
+        """frames: slot -> pinned host tensor (the slice in the ingest type, or bytes with the
+        8-bit wire).  One library call: copies, widening, masked step.  Returns the step's
+        completion handle, which also keeps the frames alive until the step is done."""
+        slots = list(frames)
+        ticket = self.batch.push_host(slots, [frames[q].data_ptr() for q in slots])
+        return _Done(self.batch, ticket, [frames[q] for q in slots])
 
     def close(self):
         self.batch.close()
+
+
+class _Done:
+    """Completion of one pool step (its ticket); holds the step's host frames until then."""
+
+    def __init__(self, batch, ticket, keep):
+        self.batch, self.ticket, self.keep = batch, ticket, keep
+
+    def query(self) -> bool:
+        if self.batch.ticket_done(self.ticket):
+            self.keep = None
+            return True
+        return False
 
 
 class Server:
@@ -244,6 +222,17 @@ class Server:
                 keep.append((ev, meta))
         self.inflight = keep
         return done
+
+    def restart_streams(self):
+        """Every admitted stream back to its initial cores, step count and statistics zero, and
+        the latency record cleared (frames still pending or in flight are dropped from it);
+        admission, pools and their device resources stay.  For starting a measurement on a
+        server whose pools have already run (first steps of a pool pay one-time costs)."""
+        for sid, (pool, slot) in self.where.items():
+            pool.reset_slot(slot, sid, self.init_cores)
+        self.latencies = []
+        self.completed = collections.defaultdict(int)
+        self.steps = 0
 
     def backlog(self) -> int:
         return sum(len(q) for q in self.pending.values()) + sum(len(m) for _, m in self.inflight)

@@ -28,7 +28,8 @@ EXPORTS = ("ttals_create", "ttals_destroy", "ttals_effective_ranks", "ttals_set_
            "ttals_launch_count", "ttals_stats_async", "ttals_profile", "ttals_profile_read",
            "ttals_slice_error_noalloc", "ttals_create_batch", "ttals_push_batch", "ttals_batch_select",
            "ttals_batch_size", "ttals_push_batch_masked", "ttals_widen_u8", "ttals_seed_cores",
-           "ttals_debug_stall_solve")
+           "ttals_debug_stall_solve", "ttals_batch_ingest_init", "ttals_batch_push_host",
+           "ttals_batch_ticket_done")
 
 
 class TTALSError(RuntimeError):
@@ -83,6 +84,9 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "ttals_batch_size": (ctypes.c_int, [VP]),
         "ttals_seed_cores": (ctypes.c_int, [VP, ctypes.c_uint64]),
         "ttals_debug_stall_solve": (ctypes.c_int, [VP, ctypes.c_int]),
+        "ttals_batch_ingest_init": (ctypes.c_int, [VP, ctypes.c_int]),
+        "ttals_batch_push_host": (ctypes.c_int, [VP, ctypes.c_int, P(ctypes.c_int), P(VP), P(ctypes.c_uint64)]),
+        "ttals_batch_ticket_done": (ctypes.c_int, [VP, ctypes.c_uint64, P(ctypes.c_int)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -250,6 +254,27 @@ class Stream:
             _check(load().ttals_push_batch_masked(self._h, ctypes.c_void_p(ptr), DTYPES[self.ingest],
                                                   ctypes.c_uint64(active), ctypes.c_void_p(stream_handle)),
                    "ttals_push_batch_masked")
+
+    def ingest_init(self, u8: bool = False):
+        """ttals_batch_ingest_init: the batch gets its own input blocks, copy/compute streams and
+        completion events (u8: frames are 8-bit pixels widened on the device)."""
+        _check(load().ttals_batch_ingest_init(self._h, 1 if u8 else 0), "ttals_batch_ingest_init")
+
+    def push_host(self, slots: Sequence[int], host_ptrs: Sequence[int]) -> int:
+        """ttals_batch_push_host: one masked step of the streams in `slots`, frame i copied from
+        pinned host address host_ptrs[i]; returns the step's ticket."""
+        n = len(slots)
+        sl = (ctypes.c_int * n)(*[int(v) for v in slots])
+        pp = (ctypes.c_void_p * n)(*[int(v) for v in host_ptrs])
+        t = ctypes.c_uint64()
+        _check(load().ttals_batch_push_host(self._h, n, sl, pp, ctypes.byref(t)), "ttals_batch_push_host")
+        return t.value
+
+    def ticket_done(self, ticket: int) -> bool:
+        d = ctypes.c_int()
+        _check(load().ttals_batch_ticket_done(self._h, ctypes.c_uint64(int(ticket)), ctypes.byref(d)),
+               "ttals_batch_ticket_done")
+        return bool(d.value)
 
     def select(self, index: int):
         """ttals_batch_select: later per-stream calls refer to stream `index` of the batch."""

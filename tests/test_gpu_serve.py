@@ -176,3 +176,42 @@ def test_seed_cores_matches_create_seed():
     b.reconstruct(out_b, "f64")
     assert torch.equal(out_a, out_b)
     assert np.array_equal(a.stats(), b.stats()) and a.step() == b.step() == 3
+
+
+def test_host_ingest_matches_masked_push():
+    """ttals_batch_push_host (the library copies the frames, widens 8-bit pixels, steps the
+    streams given a frame) computes bitwise what ttals_push_batch_masked computes on the same
+    values, and its tickets complete in order."""
+    torch = _torch()
+    from paper_2606_31061_b300.ttals import Stream
+    dims, ranks = (96, 128, 3), (32, 9, 3)
+    fr = {sid: _frames(torch, "video", {"dims": dims}, sid, 3) for sid in range(3)}
+    u8 = {sid: [torch.from_numpy(f.view(torch.float16).float().numpy().astype("uint8")).pin_memory() for f in fr[sid]]
+          for sid in fr}
+    a = Stream(dims, ranks, ingest="f16", n_streams=3)
+    b = Stream(dims, ranks, ingest="f16", n_streams=3)
+    a.ingest_init(u8=True)
+    for q in range(3):
+        for st in (a, b):
+            st.select(q)
+            st.set_cores(*_init(q, dims, st.ranks))
+    plan = [{0: 0, 1: 0, 2: 0}, {0: 1, 2: 1}, {1: 1, 2: 2}]      # slot -> frame index
+    tickets = []
+    for step in plan:
+        slots = sorted(step)
+        tickets.append(a.push_host(slots, [u8[q][step[q]].data_ptr() for q in slots]))
+        blk = torch.zeros((3,) + dims, dtype=torch.float16, device="cuda")
+        mask = 0
+        for q in slots:
+            blk[q] = fr[q][step[q]].cuda()
+            mask |= 1 << q
+        b.push_batch(blk, active=mask)
+    torch.cuda.synchronize()
+    assert tickets == [0, 1, 2] and all(a.ticket_done(t) for t in tickets)
+    for q in range(3):
+        oa, ob = (torch.empty(dims, dtype=torch.float64, device="cuda") for _ in range(2))
+        a.select(q)
+        b.select(q)
+        a.reconstruct(oa, "f64")
+        b.reconstruct(ob, "f64")
+        assert torch.equal(oa, ob) and np.array_equal(a.stats(), b.stats()) and a.step() == b.step()

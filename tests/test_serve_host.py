@@ -76,3 +76,17 @@ def test_ticks_are_masked_fifo_and_timed():
     assert s.tick() == 0
     p = serve.percentiles([3.0, 1.0, 2.0])
     assert p["p50"] == 2.0 and p["n"] == 3
+
+
+def test_restart_streams_reseeds_and_clears():
+    srv, made = _server(10_000, slots=2)
+    assert srv.connect("a", (4, 4), (2, 2)) and srv.connect("b", (4, 4), (2, 2))
+    srv.submit("a", "f0", 0.0)
+    srv.tick()
+    srv.poll(now=1.0)
+    assert srv.latencies and srv.steps == 1
+    n0 = len(made[0].resets)
+    srv.restart_streams()
+    assert srv.latencies == [] and srv.steps == 0 and not srv.completed
+    assert sorted(made[0].resets[n0:]) == [(0, "a"), (1, "b")]
+    assert srv.admitted("a") and srv.admitted("b")
