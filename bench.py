@@ -425,10 +425,12 @@ def serve_arm(seconds=2.0, n=256, lam=30.0, budget=150e9, slots=8, rank_step=16,
     def run(evts, realtime, check=False):
         srv = serve.Server(int(budget), slots=slots, rank_step=rank_step, wire="u8", init_cores=init)
         admitted = sum(srv.connect(sid, d, r) for sid, (d, r) in enumerate(specs))
-        # warm the pools (their first steps pay one-time costs), then restart every stream
+        # warm the pools (their first steps, over both input blocks and both state buffers,
+        # pay one-time costs), then restart every stream
         for sid, (d, r) in enumerate(specs):
             if srv.admitted(sid):
-                srv.submit(sid, frames[d][0], 0.0)
+                for j in range(4):
+                    srv.submit(sid, frames[d][j % len(frames[d])], 0.0)
         while srv.backlog():
             srv.tick()
             torch.cuda.synchronize()

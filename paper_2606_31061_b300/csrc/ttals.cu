@@ -353,6 +353,8 @@ struct Impl final : ttals_stream {
   float2* fXX = nullptr;       // float-float partials of ||x||^2 (solve CTAs)
   TX* fQh = nullptr;            // Q1 in the ingest type, I_1 x NP (operand of the env kernel)
   float* fW2part = nullptr;     // [8][NP*NP] W2 partials of the factor kernel's ranks
+  float* fGff = nullptr;        // [8][2][NP*NP] float-float Gram partials (ill-conditioned steps)
+  double* fL64 = nullptr;       // [8][NP*NP] FP64 factor per factor rank (ill-conditioned steps)
   float* fQfb = nullptr;
   float2* fCC = nullptr;       // float-float partials of ||x^||^2 (env CTAs)
   // environment kernel: clustered row chunks, one CTA per 64-column tile over all rows, or
@@ -586,6 +588,8 @@ struct Impl final : ttals_stream {
     TT_TRY(dalloc(&fXX, S * k1_rows * 8));            // room for the largest k-split
     TT_TRY(dalloc(&fQh, S * M * np_));
     TT_TRY(dalloc(&fW2part, S * fast::KB_CLUSTER * np_ * np_));
+    TT_TRY(dalloc(&fGff, S * fast::KB_CLUSTER * 2 * np_ * np_));
+    TT_TRY(dalloc(&fL64, S * fast::KB_CLUSTER * np_ * np_));
     TT_TRY(dalloc(&fQfb, S * M * r));
     TT_TRY(dalloc(&fHH, S * 2 * M * r));
     TT_TRY(dalloc(&fCC, S * k2_cols * k2_nq));
@@ -743,6 +747,8 @@ struct Impl final : ttals_stream {
       ab.Qfb = fQfb;
       ab.ctl = ctl_base;
       ab.fp64 = cfg_factor == 0 ? 1 : 0;
+      ab.Gff = fGff;
+      ab.L64ws = fL64;
       std::memcpy(ab.zmap, zact, sizeof(zact));
       // clusters of 8 one-CTA-per-SM CTAs fit the GPCs for up to 8 streams at once; beyond
       // that clusters of 4 (twice the rows per CTA) keep the step in one wave

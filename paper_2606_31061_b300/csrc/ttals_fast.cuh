@@ -809,7 +809,7 @@ constexpr int K1B_THREADS = 256;
 constexpr int KB_CLUSTER = 8;       // the largest factor cluster: W2-partial slab stride
 // static shared memory of k_fast_factor (W1 as float + its rounding error, L^T, the FP64
 // factor's columns, small arrays), rounded up; the launch checks dynamic + static <= 227 KB
-constexpr int K1B_STATIC_SMEM = 60 * 1024;
+constexpr int K1B_STATIC_SMEM = 76 * 1024;
 
 struct FactorArgs {
   const float* Y;         // M x r
@@ -822,6 +822,8 @@ struct FactorArgs {
   float* Qfb;             // M x r (fallback Q, float)
   Ctl* ctl;
   int fp64;               // 1: the r x r factor in FP64 (r64::ldl_factor), 0: FP32 (one warp)
+  float* Gff;             // [KB_CLUSTER][2][NP*NP] float-float Gram partials (ill-conditioned steps)
+  double* L64ws;          // [KB_CLUSTER][NP*NP] FP64 factor of each rank (ill-conditioned steps)
   unsigned char zmap[64];      // grid plane blockIdx.z -> stream (slot) of the batch
 };
 
@@ -851,6 +853,8 @@ __global__ void __launch_bounds__(K1B_THREADS, 1) k_fast_factor(FactorArgs a0) {
   a.W2part += (size_t)zs * KB_CLUSTER * NP * NP;
   a.hh_work += (size_t)zs * 2 * a.M * a.r;
   a.Qfb += (size_t)zs * a.M * a.r;
+  a.Gff += (size_t)zs * KB_CLUSTER * 2 * NP * NP;
+  a.L64ws += (size_t)zs * KB_CLUSTER * NP * NP;
   a.ctl += zs;
   extern __shared__ __align__(16) unsigned char smem[];
   constexpr int LDY = NP + 4, LQ = NP + 8, LDT = NP + 4;
@@ -861,6 +865,8 @@ __global__ void __launch_bounds__(K1B_THREADS, 1) k_fast_factor(FactorArgs a0) {
   __shared__ __align__(16) float LT[64 * 68];   // L^T: LT[k*LDT + i] = L[i][k] (zero above)
   __shared__ float dsc[64];
   __shared__ float invd[64];               // 1 / L[i][i]
+  __shared__ __align__(16) float LTlo[64 * 68];  // L - LT exactly enough for float-float (ill-conditioned steps)
+  __shared__ float invdlo[64];
   __shared__ double red[32];
   __shared__ int flags[2];                 // [0] non-finite, [1] factorisation failed
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -1079,9 +1085,58 @@ __global__ void __launch_bounds__(K1B_THREADS, 1) k_fast_factor(FactorArgs a0) {
   TTRACE(12);
   TX* Qh = (TX*)a.Qh;
   const bool fb = flags[1] != 0;      // identical in every CTA of the cluster
+  bool hh = false;
   if (fb) {
-    if (crank == 0) householder_cta<float, float>(a.Y, a.M, r, r, a.hh_work, a.Qfb, r, red);
-    cluster_sync();                   // Qfb complete before the other ranks read it
+    // A scaled pivot <= 1e-4: the local solve is ill-conditioned for the FP32 Gram and apply.
+    // FP64-accurate Cholesky-QR instead: float-float Gram of my rows (TwoProd, TwoSum), the
+    // cluster's partials summed in FP64 by every rank, the FP64 factor, a float-float apply.
+    // Only a pivot <= 1e-14 (the columns dependent to FP64 precision) takes the Householder QR.
+    float* gp = a.Gff + (size_t)crank * 2 * NP * NP;
+    for (int e = tid; e < rr; e += K1B_THREADS) {
+      const int i = e / r, j = e % r;
+      float sh = 0.f, sl = 0.f;
+      if (j <= i) {
+        for (int row = 0; row < myrows; ++row) {
+          const float yi = Ys[row * LDY + i], yj = Ys[row * LDY + j];
+          const float pr = yi * yj;
+          two_sum_acc(sh, sl, pr);
+          sl += fmaf(yi, yj, -pr);                 // pr + fma error = yi yj exactly
+        }
+      }
+      gp[e] = sh;
+      gp[NP * NP + e] = sl;
+    }
+    cluster_sync();                   // every rank's partial is in global memory
+    const auto load64 = [&](int i, int j) -> double {
+      double v = 0.0;
+      for (int q = 0; q < KBC; ++q) {
+        const float* gq = a.Gff + (size_t)q * 2 * NP * NP;
+        v += (double)__ldcg(gq + i * r + j) + (double)__ldcg(gq + NP * NP + i * r + j);
+      }
+      return v * (double)dsc[i] * (double)dsc[j];
+    };
+    double* L64 = a.L64ws + (size_t)crank * NP * NP;
+    if (tid < 128) {
+      const bool ok = r64::ldl_factor<128, NP>(r, load64, 1e-14, ldlsm, LT, LDT, nullptr, L64, NP);
+      if (!ok && tid == 0) flags[1] = 2;
+    }
+    __syncthreads();
+    hh = flags[1] == 2;               // identical in every rank (same sums, same factor)
+    if (!hh) {
+      for (int e = tid; e < rr; e += K1B_THREADS) {
+        const int i = e / r, k = e % r;
+        if (k <= i) LTlo[k * LDT + i] = (float)(L64[i * NP + k] - (double)LT[k * LDT + i]);
+      }
+      if (tid < r) {
+        const double rd = 1.0 / L64[tid * NP + tid];
+        invd[tid] = (float)rd;
+        invdlo[tid] = (float)(rd - (double)invd[tid]);
+      }
+      __syncthreads();
+    } else {
+      if (crank == 0) householder_cta<float, float>(a.Y, a.M, r, r, a.hh_work, a.Qfb, r, red);
+      cluster_sync();                 // Qfb complete before the other ranks read it
+    }
   }
   // ---- 3. Q1 rows: z = L^{-1} (D y) by forward substitution, in place in the row of Ys,
   // in 8-column register blocks (Householder Q: z = q)
@@ -1136,6 +1191,30 @@ __global__ void __launch_bounds__(K1B_THREADS, 1) k_fast_factor(FactorArgs a0) {
             *reinterpret_cast<float4*>(zr + 8 * jb + 4) = make_float4(zj[4], zj[5], zj[6], zj[7]);
           }
         }
+      } else if (!hh) {
+        // float-float forward substitution: z = L^{-1} (D y), L = LT + LTlo, 1/L_ii = invd + invdlo;
+        // the high part replaces y in place, the low part stays in zl
+        float zl[NP];
+        for (int i = 0; i < r; ++i) {
+          const float y = zr[i];
+          float sh = y * dsc[i];
+          float sl = fmaf(y, dsc[i], -sh);
+          for (int k = 0; k < i; ++k) {
+            const float lh = LT[k * LDT + i], ll = LTlo[k * LDT + i];
+            const float zh = zr[k], zlk = zl[k];
+            const float pr = lh * zh;
+            const float pe = fmaf(lh, zh, -pr) + (lh * zlk + ll * zh);
+            two_sum_acc(sh, sl, -pr);
+            sl -= pe;
+          }
+          const float rh = invd[i], rl = invdlo[i];
+          const float q = sh * rh;
+          const float qe = fmaf(sh, rh, -q) + (sh * rl + sl * rh);
+          const float zh = q + qe;
+          zl[i] = qe - (zh - q);
+          zr[i] = zh;
+        }
+        for (int c = r; c < NP; ++c) zr[c] = 0.f;
       } else {
         for (int c = 0; c < NP; ++c) zr[c] = c < r ? a.Qfb[(long long)(row0 + row) * r + c] : 0.f;
       }

@@ -345,3 +345,33 @@ def test_fused_factor_precisions(factor):
         s = st.stats()
         re_o = O.stream_relative_error(xs, xo)
         assert abs(np.sqrt(s[3] / s[2]) - re_o) <= 1e-3, (name, factor, np.sqrt(s[3] / s[2]), re_o)
+
+
+@pytest.mark.parametrize("factor", ["fp64", "fp32"])
+def test_fused_ill_conditioned_local_solves(factor):
+    """Method ranks above the data's rank make the level-1 local solve nearly rank-deficient
+    (scaled pivots below 1e-4): the fused path then takes its FP64-accurate Cholesky-QR
+    (float-float Gram and apply, FP64 factor), and for exactly low-rank data (pivots at FP64
+    rounding) the Householder QR.  Both within the FP16 ingest bar of the oracle."""
+    from paper_2606_31061_b300.ttals import Stream
+    torch = _torch()
+    cases = (("video", {"dims": (96, 128, 3), "gen_ranks": (8, 8, 3), "ranks": (24, 9, 3)}),
+             ("square", {"s": 128, "r": 32, "gen_ranks": (8, 8), "noise": 1e-4}),
+             ("square", {"s": 128, "r": 32, "gen_ranks": (8, 8), "noise": 0.0}))
+    for name, kw in cases:
+        sp = synth.make_stream(name, **kw)
+        r = O.clamp_ranks(sp.dims, sp.ranks)
+        cores, g = synth.init_cores(sp.dims, r, seed=7)
+        st = Stream(sp.dims, sp.ranks, ingest="f16", factor=factor)
+        st.set_cores(cores, g)
+        orc = O.OnlineTTALS(sp.dims, r, cores, g)
+        xs, xo = [], []
+        for x in sp.take(10):
+            dx, exact = _upload(x, "f16")
+            st.push(dx)
+            xs.append(exact)
+            xo.append(orc.step(exact))
+        s = st.stats()
+        re_o = O.stream_relative_error(xs, xo)
+        assert st.step() == 10
+        assert abs(np.sqrt(s[3] / s[2]) - re_o) <= 1e-3, (name, kw, factor, np.sqrt(s[3] / s[2]), re_o)
