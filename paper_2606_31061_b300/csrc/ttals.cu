@@ -351,6 +351,7 @@ struct Impl final : ttals_stream {
   bool finalized[2] = {true, true};
   float* fY = nullptr;
   float2* fXX = nullptr;       // float-float partials of ||x||^2 (solve CTAs)
+  float2* fW1 = nullptr;       // [row tiles][NP*NP] float-float Gram partials of Y (solve CTAs)
   TX* fQh = nullptr;            // Q1 in the ingest type, I_1 x NP (operand of the env kernel)
   float* fW2part = nullptr;     // [8][NP*NP] W2 partials of the factor kernel's ranks
   float* fGff = nullptr;        // [8][2][NP*NP] float-float Gram partials (ill-conditioned steps)
@@ -565,8 +566,12 @@ struct Impl final : ttals_stream {
       case 48: k1_smem = fast::k1_smem_bytes<48>(); break;
       default: k1_smem = fast::k1_smem_bytes<64>(); break;
     }
-    // after the main loop the solve CTA reuses its buffers: P (64 x NP), Gram (r x r), rows
-    k1_smem = std::max(k1_smem, (size_t)(64 * np_ + r * r + 64 * r) * 4 + 64);
+    // after the main loop the solve CTA reuses its buffers: P (64 x NP), its reduced rows
+    // (64 x (NP+4)), the Gram's row-group partials and the Gram (NP x NP each); + alignment
+    {
+      const int ng = std::max(1, fast::K1_THREADS / ((np_ / 4) * (np_ / 4)));
+      k1_smem = std::max(k1_smem, (size_t)(64 * np_ + 64 * (np_ + 4) + (ng + 1) * np_ * np_) * 4 + 1024);
+    }
     if (k2_smem > 226 * 1024 || k2_rch > 256) return TTALS_OK;
     if (!tensor_map_encoder()) return TTALS_OK;
     switch (np_) {
@@ -586,6 +591,7 @@ struct Impl final : ttals_stream {
     TT_TRY(dalloc(&fShiftb, S * 2));
     TT_TRY(dalloc(&fY, S * M * r));
     TT_TRY(dalloc(&fXX, S * k1_rows * 8));            // room for the largest k-split
+    TT_TRY(dalloc(&fW1, S * k1_rows * np_ * np_));    // room for the 64-row tiles
     TT_TRY(dalloc(&fQh, S * M * np_));
     TT_TRY(dalloc(&fW2part, S * fast::KB_CLUSTER * np_ * np_));
     TT_TRY(dalloc(&fGff, S * fast::KB_CLUSTER * 2 * np_ * np_));
@@ -702,6 +708,8 @@ struct Impl final : ttals_stream {
       a1.kchunk = kchunk;
       a1.Y = fY;
       a1.xx_part = fXX;
+      a1.W1part = fW1;
+      a1.w1_stride = (long long)k1_rows * NP * NP;
       a1.ctl = ctl_base;
       std::memcpy(a1.zmap, zact, sizeof(zact));
       cudaLaunchConfig_t c1{};
@@ -713,6 +721,7 @@ struct Impl final : ttals_stream {
       c1.numAttrs = 2;
       TT_TRY(mark(1, s));
       int nxx = k1_rows * split;               // ||x||^2 partials per stream
+      int nw1 = k1_rows;                       // Gram partials per stream (row tiles)
       // tcgen05 over whole rows once its 128-row tiles of the stepping streams cover three
       // quarters of the SMs (one CTA per SM); below that the k-split mma.sync kernel fills
       // the GPU better
@@ -728,6 +737,7 @@ struct Impl final : ttals_stream {
         c1.numAttrs = 1;
         TT_CUDA(cudaLaunchKernelEx(&c1, fast::k_fast_solve_tc<TX, NP>, maps[2], mapB[par], a1));
         nxx = rows_tc;
+        nw1 = rows_tc;
       } else {
         TT_CUDA(cudaLaunchKernelEx(&c1, fast::k_fast_solve<TX, NP>, mapX1, mapB[par], a1));
       }
@@ -738,6 +748,9 @@ struct Impl final : ttals_stream {
       ab.Y = fY;
       ab.xx_part = fXX;
       ab.nxx = nxx;
+      ab.W1part = fW1;
+      ab.w1_stride = a1.w1_stride;
+      ab.nw1 = nw1;
       ab.M = (int)dims[0];
       ab.r = r;
       ab.Qh = fQh;

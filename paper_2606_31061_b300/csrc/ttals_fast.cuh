@@ -267,11 +267,60 @@ struct SolveArgs {
   long long K, kchunk;    // kchunk % K1_BK == 0
   float* Y;               // M x r
   float2* xx_part;        // [row tiles * splits] float-float partials of ||x||^2
+  float2* W1part;         // [row tiles][NP*NP] float-float Gram partials Y_t^T Y_t of the row tiles
+  long long w1_stride;    // float2 elements per stream of W1part
   Ctl* ctl;
   int stall;              // fault injection (k_fast_solve): issue no copy, so that the
                           // consumers' first bounded wait runs out (0 in normal use)
   unsigned char zmap[64];      // grid plane blockIdx.z -> stream (slot) of the batch
 };
+
+// Gram of a row tile for the factor of the local solve (Sec. 3.4.2: QR of G~ through the
+// Cholesky factor of G~^T G~): G = Yt^T Yt over the nrows rows of a row-major tile (row i at
+// Yt + i * ldy, 16-byte aligned rows, NP columns, zero past r) by the NT threads of the block,
+// in FP32 4 x 4 register blocks.  The rows are split into NRG groups whose partials (Gr: NRG
+// NP x NP matrices of shared memory; Gr may be G when NRG = 1) are summed in group order into
+// G.  Yt must be complete before the call; the function ends with a block barrier.
+template <int NP, int NT>
+__host__ __device__ constexpr int tile_gram_groups() {
+  return NT / ((NP / 4) * (NP / 4)) > 0 ? NT / ((NP / 4) * (NP / 4)) : 1;
+}
+template <int NP, int NT>
+__device__ __forceinline__ void tile_gram(const float* Yt, int ldy, int nrows, float* Gr, float* G) {
+  constexpr int NB = NP / 4, NBLK = NB * NB, NRG = tile_gram_groups<NP, NT>();
+  const int tid = threadIdx.x;
+  for (int w = tid; w < NRG * NBLK; w += NT) {
+    const int blk = w % NBLK, rg = w / NBLK, ib = blk / NB, jb = blk % NB;
+    float acc[4][4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int v = 0; v < 4; ++v) acc[u][v] = 0.f;
+    for (int row = rg; row < nrows; row += NRG) {
+      const float4 yi = *reinterpret_cast<const float4*>(Yt + row * ldy + 4 * ib);
+      const float4 yj = *reinterpret_cast<const float4*>(Yt + row * ldy + 4 * jb);
+      const float vi[4] = {yi.x, yi.y, yi.z, yi.w}, vj[4] = {yj.x, yj.y, yj.z, yj.w};
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc[u][v] = fmaf(vi[u], vj[v], acc[u][v]);
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int v = 0; v < 4; ++v) Gr[rg * NP * NP + (4 * ib + u) * NP + 4 * jb + v] = acc[u][v];
+  }
+  __syncthreads();
+  if (NRG > 1 || Gr != G) {
+    for (int e = tid; e < NP * NP; e += NT) {
+      float s = 0.f;
+#pragma unroll
+      for (int g = 0; g < NRG; ++g) s += Gr[g * NP * NP + e];
+      G[e] = s;
+    }
+    __syncthreads();
+  }
+}
 
 template <int NP>
 __host__ __device__ constexpr int k1_stages() { return NP <= 32 ? 4 : 3; }
@@ -479,15 +528,44 @@ __global__ void __launch_bounds__(K1_THREADS, 2)
   }
   cluster_sync();
   if (tr0) TTRACE(2);
-  // ---- rank q reduces rows [q*rpc, (q+1)*rpc) over the cluster in fixed rank order
+  // ---- rank q reduces rows [q*rpc, (q+1)*rpc) over the cluster in fixed rank order, writes
+  // them to Y and keeps them (Yr, zero past r and past I_1) for the Gram partial
   const int rpc = K1_BM / nsplit;
   const int rbeg = (int)crank * rpc;
   const uint32_t Pbase = smem_u32(P);
-  for (int e = tid; e < rpc * r; e += K1_THREADS) {
-    const int lr = e / r, c = e % r;
+  constexpr int LDR = NP + 4;
+  float* Yr = P + K1_BM * NP;                                   // [rpc][LDR]
+  float* Gr = Yr + K1_BM * LDR;                                 // row-group partials
+  float* G = Gr + tile_gram_groups<NP, K1_THREADS>() * NP * NP;  // Gram of my rows
+  for (int e = tid; e < rpc * NP; e += K1_THREADS) {
+    const int lr = e / NP, c = e % NP;
     const int row = rbeg + lr;
-    const float s = dsmem_sum8(Pbase + (uint32_t)(row * NP + c) * 4u, nsplit);
-    if (m0 + row < a.M) a.Y[(long long)(m0 + row) * r + c] = s;
+    const bool in = c < r && m0 + row < a.M;
+    const float s = c < r ? dsmem_sum8(Pbase + (uint32_t)(row * NP + c) * 4u, nsplit) : 0.f;
+    if (in) a.Y[(long long)(m0 + row) * r + c] = s;
+    Yr[lr * LDR + c] = in ? s : 0.f;
+  }
+  __syncthreads();
+  tile_gram<NP, K1_THREADS>(Yr, LDR, rpc, Gr, G);
+  float2* W1t = a.W1part + (size_t)zs * a.w1_stride + (size_t)rt * NP * NP;
+  if (nsplit == 1) {
+    for (int e = tid; e < NP * NP; e += K1_THREADS) W1t[e] = make_float2(G[e], 0.f);
+  } else {
+    cluster_sync();   // every rank's Gram is complete (and every rank has read the P tiles)
+    // the row tile's Gram: entries [q*per, (q+1)*per) summed over the ranks in rank order
+    // (TwoSum: a float-float pair)
+    const int per = NP * NP / nsplit;
+    const uint32_t Gbase = smem_u32(G);
+    for (int e = tid; e < per; e += K1_THREADS) {
+      const int ge = (int)crank * per + e;
+      float v[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) v[q] = dsmem_ld_rank(Gbase + (uint32_t)ge * 4u, q, nsplit);
+      float hi = 0.f, lo = 0.f;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) two_sum_acc(hi, lo, v[q]);
+      W1t[ge] = make_float2(hi, lo);
+    }
   }
   cluster_sync();   // peers' shared memory stays valid until every rank has read it
   TTRACE_CTA(3);
@@ -762,22 +840,37 @@ __global__ void __launch_bounds__(K1T_THREADS, 1)
       if (lane == 0) mbar_arrive(smem_u32(&empty[st]));
     }
   }
-  // ---- epilogue: the accumulator -> Y (warps 2-5: TMEM lanes 32 (warp % 4) ..)
+  // ---- epilogue: the accumulator -> the tile Ys in shared memory over the stage buffers,
+  // which are free once every MMA has completed (warps 2-5: TMEM lanes 32 (warp % 4) ..;
+  // zero past r and past I_1)
+  constexpr int LDY = NP + 4;
+  static_assert((size_t)(K1T_BM * LDY + (tile_gram_groups<NP, K1T_THREADS>() + 1) * NP * NP) * 4 <=
+                    (size_t)ST * k1t_stage_bytes<NP>(), "epilogue tiles fit the stage buffers");
+  float* Ys = reinterpret_cast<float*>(smem);                  // [128][LDY]
+  float* Gr = Ys + K1T_BM * LDY;                               // row-group partials
+  float* G = Gr + tile_gram_groups<NP, K1T_THREADS>() * NP * NP;
   if (warp >= 2) {
     const bool ok = mbar_wait(smem_u32(&done), 0);
     if (!ok) timeout_flag = 1;
     tc_fence_after();
     const int q = warp & 3;                    // TMEM lane quarter of this warp
     const int row = q * 32 + lane;
-    const int grow = m0 + row;
+    const bool in = m0 + row < a.M;
     float v[32];
 #pragma unroll
     for (int c0 = 0; c0 < NP; c0 += 32) {
       tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, v);
-      if (ok && grow < a.M) {
+      if (ok) {
 #pragma unroll
-        for (int j = 0; j < 32; ++j)
-          if (c0 + j < r) a.Y[(long long)grow * r + c0 + j] = v[j];
+        for (int j4 = 0; j4 < 8; ++j4)
+          if (c0 + 4 * j4 < NP) {
+            float4 w;
+            w.x = (in && c0 + 4 * j4 + 0 < r) ? v[4 * j4 + 0] : 0.f;
+            w.y = (in && c0 + 4 * j4 + 1 < r) ? v[4 * j4 + 1] : 0.f;
+            w.z = (in && c0 + 4 * j4 + 2 < r) ? v[4 * j4 + 2] : 0.f;
+            w.w = (in && c0 + 4 * j4 + 3 < r) ? v[4 * j4 + 3] : 0.f;
+            *reinterpret_cast<float4*>(Ys + row * LDY + c0 + 4 * j4) = w;
+          }
       }
     }
   }
@@ -789,6 +882,16 @@ __global__ void __launch_bounds__(K1T_THREADS, 1)
     if (timeout_flag) a.ctl->latched = 5;
   }
   __syncthreads();
+  if (!timeout_flag) {      // block-uniform here
+    // the tile's rows of Y, coalesced (rows of Y are contiguous)
+    const int nrow = a.M - m0 < K1T_BM ? a.M - m0 : K1T_BM;
+    for (int e = tid; e < nrow * r; e += K1T_THREADS) a.Y[(long long)m0 * r + e] = Ys[(e / r) * LDY + e % r];
+    // the tile's Gram partial (FP32 over its 128 rows; lo part zero)
+    tile_gram<NP, K1T_THREADS>(Ys, LDY, K1T_BM, Gr, G);
+    float2* W1t = a.W1part + (size_t)zs * a.w1_stride + (size_t)rt * NP * NP;
+    for (int e = tid; e < NP * NP; e += K1T_THREADS) W1t[e] = make_float2(G[e], 0.f);
+  }
+  __syncthreads();
   tc_fence_after();
   if (warp == 1) tmem_dealloc(tmem, TCOLS);
 }
@@ -796,8 +899,8 @@ __global__ void __launch_bounds__(K1T_THREADS, 1)
 // ================================================================ K1b: r x r factor
 // A cluster of KBC (8, or 4 for large batches) CTAs; CTA q owns rows [q*nrows, (q+1)*nrows)
 // of Y.
-//  1. Gram partial of my rows (FP32, 4 x 4 register blocks), W1 = the ranks' partials
-//     summed in rank order by every rank through distributed shared memory.
+//  1. W1 = Y^T Y: every rank sums the solve kernel's row-tile Gram partials in tile order
+//     (float-float) while its rows of Y are still arriving.
 //  2. Every rank factors the scaled Gram D W1 D = L L^T (FP32, one warp).
 //  3. Q1 = Y D L^{-T}: each thread forward-substitutes whole rows, z = L^{-1} (D y),
 //     and rounds them to the ingest type (the values that multiply X in the env kernel).
@@ -814,6 +917,9 @@ constexpr int K1B_STATIC_SMEM = 76 * 1024;
 struct FactorArgs {
   const float* Y;         // M x r
   const float2* xx_part;  // [nxx] float-float partials of ||x||^2
+  const float2* W1part;   // [nw1][NP*NP] float-float Gram partials of Y's row tiles (solve kernel)
+  long long w1_stride;    // float2 elements per stream of W1part
+  int nw1;
   int nxx, M, r;
   void* Qh;               // M x NP ingest-type Q1 (columns >= r zero)
   float* Qst;             // state: Q1 (M x r) as float
@@ -829,15 +935,11 @@ struct FactorArgs {
 
 // rows of Y handled by one CTA of a factor cluster of kbc CTAs
 __host__ __device__ constexpr int k1b_rows(int M, int kbc = KB_CLUSTER) { return ((M + kbc - 1) / kbc + 15) / 16 * 16; }
-// row groups of the Gram partial: 4 x 4 blocks of an NP x NP Gram per thread
-__host__ __device__ constexpr int k1b_rgroups(int np) {
-  return K1B_THREADS / ((np / 4) * (np / 4)) > 0 ? K1B_THREADS / ((np / 4) * (np / 4)) : 1;
-}
 // dynamic shared memory: Y rows (fp32, stride NP+4) | Q1 rows (ingest type, stride NP+8) |
-// Gram partials of the row groups | this rank's Gram partial (W1, later W2)
+// this rank's W2 partial
 __host__ __device__ constexpr size_t k1b_smem_bytes(int M, int r, int np, int kbc = KB_CLUSTER) {
   return (size_t)k1b_rows(M, kbc) * (np + 4) * 4 + (size_t)(k1b_rows(M, kbc) + 16) * (np + 8) * 2 +
-         (size_t)k1b_rgroups(np) * np * np * 4 + (size_t)np * np * 4 + 256 + 0 * r;
+         (size_t)np * np * 4 + 256 + 0 * r;
 }
 
 template <typename TX, int NP, int KBC>
@@ -848,6 +950,7 @@ __global__ void __launch_bounds__(K1B_THREADS, 1) k_fast_factor(FactorArgs a0) {
   FactorArgs a = a0;
   a.Y += (size_t)zs * a.M * a.r;
   a.xx_part += (size_t)zs * a.nxx;
+  a.W1part += (size_t)zs * a.w1_stride;
   a.Qh = (void*)((TX*)a.Qh + (size_t)zs * a.M * NP);
   a.Qst += (size_t)zs * a.M * a.r;
   a.W2part += (size_t)zs * KB_CLUSTER * NP * NP;
@@ -858,7 +961,6 @@ __global__ void __launch_bounds__(K1B_THREADS, 1) k_fast_factor(FactorArgs a0) {
   a.ctl += zs;
   extern __shared__ __align__(16) unsigned char smem[];
   constexpr int LDY = NP + 4, LQ = NP + 8, LDT = NP + 4;
-  constexpr int NB = NP / 4, NBLK = NB * NB, NRG = k1b_rgroups(NP);
   __shared__ float W[64 * 64];             // W1 (FP32 rounding of its float-float sum)
   __shared__ float Wlo[64 * 64];           // W1 - W exactly: W1 = W + Wlo (the FP64 factor's input)
   __shared__ r64::Smem ldlsm;
@@ -877,8 +979,7 @@ __global__ void __launch_bounds__(K1B_THREADS, 1) k_fast_factor(FactorArgs a0) {
   const int myrows = (a.M - row0 < nrows) ? (a.M - row0 > 0 ? a.M - row0 : 0) : nrows;
   float* Ys = reinterpret_cast<float*>(smem);                               // [nrows][LDY]
   TX* Qs = reinterpret_cast<TX*>(Ys + (size_t)nrows * LDY);                 // [nrows+16][LQ]
-  float* Gr = reinterpret_cast<float*>(Qs + (size_t)(nrows + 16) * LQ);     // [NRG][NP*NP]
-  float* Wp = Gr + NRG * NP * NP;                                          // [NP*NP]
+  float* Wp = reinterpret_cast<float*>(Qs + (size_t)(nrows + 16) * LQ);     // [NP*NP]
   pdl_wait();
   pdl_trigger();
   TTRACE(10);
@@ -918,70 +1019,51 @@ __global__ void __launch_bounds__(K1B_THREADS, 1) k_fast_factor(FactorArgs a0) {
       if (crank == 0 && !flags[0]) a.ctl->xx = xs;   // a skipped step keeps the committed value
     }
   }
-  cp_async_wait<0>();
+  // ---- 1. W1 = sum of the row tiles' Gram partials in tile order (float-float).  Thread t
+  // owns the packed lower-triangle entries t, t + 256, ...; all its loads of a batch of
+  // partials are issued together (one L2 round trip per batch), then summed in tile order.
+  {
+    constexpr int NE = NP * (NP + 1) / 2, U = (NE + K1B_THREADS - 1) / K1B_THREADS;
+    constexpr int PB = 54 / U > 0 ? 54 / U : 1;    // partials per batch: ~54 loads in flight
+    const int ne = r * (r + 1) / 2;
+    int off[U];
+    float hi[U], lo[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int e = tid + u * K1B_THREADS;
+      int i = (int)((sqrtf(8.f * (float)e + 1.f) - 1.f) * 0.5f);
+      while (i > 0 && i * (i + 1) / 2 > e) --i;
+      while ((i + 1) * (i + 2) / 2 <= e) ++i;
+      off[u] = e < ne ? i * NP + (e - i * (i + 1) / 2) : -1;
+      hi[u] = 0.f;
+      lo[u] = 0.f;
+    }
+    for (int t0 = 0; t0 < a.nw1; t0 += PB) {
+      float2 v[U][PB];
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+#pragma unroll
+        for (int q = 0; q < PB; ++q)
+          v[u][q] = (off[u] >= 0 && t0 + q < a.nw1) ? __ldcg(a.W1part + (size_t)(t0 + q) * NP * NP + off[u])
+                                                    : make_float2(0.f, 0.f);
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+#pragma unroll
+        for (int q = 0; q < PB; ++q) ff_add(hi[u], lo[u], v[u][q].x, v[u][q].y);
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (off[u] >= 0) {
+        const int i = off[u] / NP, j = off[u] % NP;
+        const float w = hi[u] + lo[u], wl = (hi[u] - w) + lo[u];   // exact split (|lo| <= ulp(hi) / 2)
+        W[i * r + j] = w;
+        Wlo[i * r + j] = wl;
+        W[j * r + i] = w;
+        Wlo[j * r + i] = wl;
+      }
+  }
   __syncthreads();
   TTRACE(16);
-  // ---- 1. Gram partial: thread (row group, 4 x 4 block); row groups summed in order
-  if (tid < NRG * NBLK) {
-    const int blk = tid % NBLK, rg = tid / NBLK, ib = blk / NB, jb = blk % NB;
-    float acc[4][4];
-#pragma unroll
-    for (int u = 0; u < 4; ++u)
-#pragma unroll
-      for (int w = 0; w < 4; ++w) acc[u][w] = 0.f;
-    for (int row = rg; row < myrows; row += NRG) {
-      const float4 yi = *reinterpret_cast<const float4*>(Ys + row * LDY + 4 * ib);
-      const float4 yj = *reinterpret_cast<const float4*>(Ys + row * LDY + 4 * jb);
-      const float vi[4] = {yi.x, yi.y, yi.z, yi.w}, vj[4] = {yj.x, yj.y, yj.z, yj.w};
-#pragma unroll
-      for (int u = 0; u < 4; ++u)
-#pragma unroll
-        for (int w = 0; w < 4; ++w) acc[u][w] = fmaf(vi[u], vj[w], acc[u][w]);
-    }
-#pragma unroll
-    for (int u = 0; u < 4; ++u)
-#pragma unroll
-      for (int w = 0; w < 4; ++w) Gr[rg * NP * NP + (4 * ib + u) * NP + 4 * jb + w] = acc[u][w];
-  }
-  __syncthreads();
-  for (int e = tid; e < NP * NP; e += K1B_THREADS) {
-    float sum = 0.f;
-#pragma unroll
-    for (int g = 0; g < NRG; ++g) sum += Gr[g * NP * NP + e];
-    Wp[e] = sum;
-  }
-  TTRACE(17);
-  cluster_sync();
-  {
-    const uint32_t wb = smem_u32(Wp);
-    for (int e0 = tid; e0 < rr; e0 += 4 * K1B_THREADS) {
-      float v[4][KBC];
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int e = e0 + u * K1B_THREADS;
-        const int ec = e < rr ? e : rr - 1;            // in-range address; value masked below
-        const uint32_t la = wb + (uint32_t)((ec / r) * NP + ec % r) * 4u;
-#pragma unroll
-        for (int q = 0; q < KBC; ++q) {
-          const float x = dsmem_ld_rank(la, q, KBC);
-          v[u][q] = e < rr ? x : 0.f;
-        }
-      }
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        float hi = 0.f, lo = 0.f;
-#pragma unroll
-        for (int q = 0; q < KBC; ++q) two_sum_acc(hi, lo, v[u][q]);
-        if (e0 + u * K1B_THREADS < rr) {
-          const float w = hi + lo;
-          W[e0 + u * K1B_THREADS] = w;
-          Wlo[e0 + u * K1B_THREADS] = (hi - w) + lo;     // exact (|lo| <= ulp(hi) / 2)
-        }
-      }
-    }
-  }
-  cluster_arrive();     // my partial may be released once every rank has read it (wait below)
-  __syncthreads();
   for (int e = tid; e < rr; e += K1B_THREADS)
     if (!isfinite(W[e])) flags[0] = 1;
   if (tid < 64) {
@@ -997,7 +1079,7 @@ __global__ void __launch_bounds__(K1B_THREADS, 1) k_fast_factor(FactorArgs a0) {
     if (flags[0] && a.ctl->latched != 5) a.ctl->latched = 4;   // a solve timeout stays ETIMEOUT
   }
   if (flags[0]) {           // uniform across the cluster (identical W1 and ||x||^2)
-    cluster_wait();
+    cp_async_wait<0>();
     return;
   }
   TTRACE(11);
@@ -1080,7 +1162,7 @@ __global__ void __launch_bounds__(K1B_THREADS, 1) k_fast_factor(FactorArgs a0) {
         }
     }
   }
-  cluster_wait();           // every rank has read W1's partials
+  cp_async_wait<0>();       // my rows of Y
   __syncthreads();
   TTRACE(12);
   TX* Qh = (TX*)a.Qh;
