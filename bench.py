@@ -345,7 +345,8 @@ def c4_arm(steps, depth=4, tune=True):
     sched = {}
     for b in grp.buckets:
         key = f"{b.dims[0]}x{b.dims[1]} r{b.ranks[0]} n{len(b.members)}"
-        sched[key] = {k: v for k, v in b.schedule.items() if k in ("env_kernel", "k1_split")}
+        sched[key] = {k: v for k, v in b.schedule.items() if k in ("env_kernel", "solve_kernel", "k1_split",
+                                                                    "factor_cluster")}
     out = {
         "workload": "64 streams, s x s slices with s ~ U{128,256,512,1024}, ranks (r, r) with r ~ U{8,16,32,64} "
                     "(seed 1004), drifting low-rank TT fields + noise 0.01, FP16 ingest",

@@ -88,6 +88,13 @@ typedef struct {
                             FP64, then the QR of Sec. 3.4.2), 2 = noortho (the ablation of
                             Sec. 5.4: LQ/QR removed, both Gram inverses, FP64 r x r solves).
                             1 and 2 run on the generic path (no batches).                 */
+    int solve_kernel;    /* fused path, local-solve kernel and its tile shape (S4): 0 = chosen
+                            per launch from the stepping streams' row tiles, 1 = mma.sync on
+                            64-row tiles with k-splits (k1_split) reduced in a cluster, 2 =
+                            tcgen05 on 128-row tiles over whole rows (no k-split)          */
+    int factor_cluster;  /* fused path, CTAs per stream of the r x r factor kernel (S5): 0 =
+                            chosen by batch size, 4 or 8 (rows of Y per CTA: I_1/4 or I_1/8;
+                            4 only where its shared memory fits, else 8)                   */
 } ttals_config;
 
 /*
@@ -101,8 +108,9 @@ typedef struct {
  * ("Initialize orthogonal cores randomly", Algorithm 1): Gaussian entries from a
  * SplitMix64 / Box-Muller generator seeded with cfg->seed.  Allocates every
  * device buffer the update needs; no later call allocates.
- * env_kernel and k1_split fix the fused path's schedule (an autotuner's choice); they change
- * the FP32 summation order, never the arithmetic the update performs.
+ * env_kernel, k1_split, solve_kernel and factor_cluster fix the fused path's schedule (an
+ * autotuner's choice); they change the FP32 summation order, never the arithmetic the update
+ * performs.
  * Errors: EINVAL (shape, dtype, schedule fields out of range, reserved fields), ENOMEM,
  * ECUDA.  On error *out is NULL.
  */

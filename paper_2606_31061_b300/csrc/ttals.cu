@@ -184,6 +184,8 @@ struct ttals_stream {
   unsigned long long active_mask = ~0ull;   // streams of a batch that take the next push
   int cfg_env_kernel = 0;             // ttals_config.env_kernel (0: by shape)
   int cfg_k1_split = 0;               // ttals_config.k1_split (0: by shape and batch)
+  int cfg_solve_kernel = 0;           // ttals_config.solve_kernel (0: per launch)
+  int cfg_factor_cluster = 0;         // ttals_config.factor_cluster (0: by batch size)
   int cfg_factor = 0;                 // ttals_config.factor (0: FP64 r x r factor, 1: FP32)
   int mode = 0;                       // ttals_config.mode: 0 literal, 1 lsq, 2 noortho
   size_t bytes = 0;
@@ -528,6 +530,8 @@ struct Impl final : ttals_stream {
       }
       // TTALS_SOLVE_KERNEL=tc|mma fixes the local-solve kernel (else chosen per launch)
       if (const char* e = std::getenv("TTALS_SOLVE_KERNEL")) k1_tc = std::string(e) == "tc" ? 1 : -1;
+      if (cfg_solve_kernel == 1) k1_tc = -1;                  // the stream's config wins
+      else if (cfg_solve_kernel == 2) k1_tc = 1;
       if (cfg_env_kernel == 1) k2_kind = K2_CLUSTER;          // the stream's config wins
       else if (cfg_env_kernel == 2 && fits) k2_kind = K2_SINGLE;
       else if (cfg_env_kernel == 3) k2_kind = K2_STREAM;
@@ -765,7 +769,10 @@ struct Impl final : ttals_stream {
       std::memcpy(ab.zmap, zact, sizeof(zact));
       // clusters of 8 one-CTA-per-SM CTAs fit the GPCs for up to 8 streams at once; beyond
       // that clusters of 4 (twice the rows per CTA) keep the step in one wave
-      const int kbc = (n_act > 8 && fast::k1b_smem_bytes((int)dims[0], r, NP, 4) + fast::K1B_STATIC_SMEM <= 227 * 1024) ? 4 : 8;
+      const bool fits4 = fast::k1b_smem_bytes((int)dims[0], r, NP, 4) + fast::K1B_STATIC_SMEM <= 227 * 1024;
+      int kbc = (n_act > 8 && fits4) ? 4 : 8;
+      if (cfg_factor_cluster == 4 && fits4) kbc = 4;          // a configured cluster size wins
+      else if (cfg_factor_cluster == 8) kbc = 8;
       cudaLaunchAttribute atb[2];
       atb[0] = at[0];
       atb[0].val.clusterDim.y = (unsigned)kbc;
@@ -1488,6 +1495,8 @@ static ttals_status create_streams(int nbatch, int n_slice_modes, const int64_t*
     if (c.env_kernel < 0 || c.env_kernel > 4) return TTALS_EINVAL;
     if (c.k1_split != 0 && c.k1_split != 1 && c.k1_split != 2 && c.k1_split != 4 && c.k1_split != 8)
       return TTALS_EINVAL;
+    if (c.solve_kernel < 0 || c.solve_kernel > 2) return TTALS_EINVAL;
+    if (c.factor_cluster != 0 && c.factor_cluster != 4 && c.factor_cluster != 8) return TTALS_EINVAL;
     if (c.seed == 0) c.seed = 0x5eedull;
   }
   if (c.ingest < TTALS_F64 || c.ingest > TTALS_BF16) return TTALS_EINVAL;
@@ -1542,6 +1551,8 @@ static ttals_status create_streams(int nbatch, int n_slice_modes, const int64_t*
   s->nbatch = nbatch;
   s->cfg_env_kernel = c.env_kernel;
   s->cfg_k1_split = c.k1_split;
+  s->cfg_solve_kernel = c.solve_kernel;
+  s->cfg_factor_cluster = c.factor_cluster;
   s->cfg_factor = c.factor;
   s->mode = c.mode;
   if (cudaEventCreateWithFlags(&s->ev, cudaEventDisableTiming) != cudaSuccess) {

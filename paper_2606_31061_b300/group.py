@@ -8,8 +8,9 @@ caller's stream: their latency-bound kernel chains overlap on the GPU.  ``captur
 an even number of steps into one CUDA graph (K parallel branches per step), so that a
 replay costs one graph launch.
 
-Each batch's schedule (environment kernel kind, k-splits of the local solve) comes from
-``tune.best_schedule`` unless ``tune=False``.  The schedule changes only the order of FP32
+Each batch's schedule (environment kernel and local-solve kernel with their tile shapes,
+k-splits of the local solve, factor cluster size) comes from ``tune.best_schedule`` unless
+``tune=False``.  The schedule changes only the order of FP32
 sums, never what is computed.
 
 Inputs live in device memory owned by the group: for every batch a ring of ``depth``
@@ -53,9 +54,9 @@ class _Bucket:
         self.members = list(members)            # group stream indices, in slot order
         self.schedule = dict(schedule or {})
         n = len(self.members)
+        from .tune import KEYS
         self.stream = Stream(dims, ranks, ingest=ingest, n_streams=n,
-                             env_kernel=self.schedule.get("env_kernel", 0),
-                             k1_split=self.schedule.get("k1_split", 0))
+                             **{k: int(self.schedule.get(k, 0)) for k in KEYS})
         dt = getattr(torch, _TORCH_DT[ingest])
         self.inputs = torch.zeros((depth, n) + self.dims, dtype=dt, device="cuda")
 

@@ -42,7 +42,8 @@ class TTALSError(RuntimeError):
 class Config(ctypes.Structure):
     _fields_ = [("ingest", ctypes.c_int), ("seed", ctypes.c_uint64), ("device", ctypes.c_int),
                 ("qr_passes", ctypes.c_int), ("env_kernel", ctypes.c_int), ("k1_split", ctypes.c_int),
-                ("factor", ctypes.c_int), ("mode", ctypes.c_int)]
+                ("factor", ctypes.c_int), ("mode", ctypes.c_int), ("solve_kernel", ctypes.c_int),
+                ("factor_cluster", ctypes.c_int)]
 
 
 _lib = None
@@ -122,7 +123,8 @@ class Stream:
 
     def __init__(self, dims: Sequence[int], ranks: Sequence[int], ingest: str = "f64",
                  seed: int = 0x5EED, device: int = 0, qr_passes: int = 0, n_streams: int = 0,
-                 env_kernel: int = 0, k1_split: int = 0, factor: str = "fp64", mode: str = "literal"):
+                 env_kernel: int = 0, k1_split: int = 0, factor: str = "fp64", mode: str = "literal",
+                 solve_kernel: int = 0, factor_cluster: int = 0):
         lib = load()
         self.dims = tuple(int(d) for d in dims)
         self.ingest = ingest
@@ -131,7 +133,7 @@ class Stream:
         if mode not in MODES:
             raise ValueError(f"mode must be one of {sorted(MODES)}, not {mode!r}")
         cfg = Config(DTYPES[ingest], seed, device, qr_passes, env_kernel, k1_split, 0 if factor == "fp64" else 1,
-                     MODES[mode])
+                     MODES[mode], solve_kernel, factor_cluster)
         h = ctypes.c_void_p()
         if n_streams > 0:
             code = lib.ttals_create_batch(int(n_streams), len(self.dims), _i64(self.dims), _i64(ranks),

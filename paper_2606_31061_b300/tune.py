@@ -1,13 +1,24 @@
-"""Autotuner of the fused path's schedule for a batch shape.
+"""Autotuner of the fused path's schedule and tile shapes for a batch shape.
 
-A schedule is the environment kernel kind (``env_kernel``: 1 clustered, 2 one CTA per
-column tile over all rows, 3 streamed row stages, 4 streamed row stages on tcgen05) and the
-number of k-splits of the local solve (``k1_split``: 1, 2, 4, 8).  For a shape (slice dims, ranks, ingest, batch size) the
-tuner times every environment kind at the default split, then every split with the best
-kind, each on seeded synthetic slices (device-timed with CUDA events over a few pushes,
-after warm-up), and keeps the fastest.  Results are cached per shape for the process.
-A kind that does not fit the shape falls back to the library's own choice, so the same
-schedule may be timed twice; the cache key makes that harmless.
+A schedule fixes, per batch:
+
+* ``env_kernel``, the environment kernel and its tile: 1 clustered (128-column tiles, row
+  chunks reduced in a cluster), 2 one CTA per 64-column tile over all rows, 3 streamed 64-row
+  stages of a 128-column tile, 4 the same on tcgen05;
+* ``solve_kernel`` with ``k1_split``, the local-solve kernel and its tile: 2 tcgen05 over
+  whole 128-row tiles, or 1 mma.sync on 64-row tiles split 1, 2, 4 or 8 ways along the
+  contraction (the splits of a tile reduced in a cluster);
+* ``factor_cluster``, the CTAs per stream of the r x r factor kernel (4 or 8: I_1/4 or I_1/8
+  rows of Y per CTA).
+
+For a shape (slice dims, ranks, ingest, batch size) the tuner descends one coordinate at a
+time: every environment kind with the library's defaults, then every solve tile with the best
+kind, then both factor clusters with the best of those; each candidate is timed on seeded
+synthetic slices (device-timed with CUDA events over a few pushes, after warm-up) and the
+fastest of all timed candidates is kept.  Results are cached per shape for the process.  A
+choice that does not fit the shape falls back to the library's own, so the same schedule
+may be timed twice; the cache key makes that harmless.  No choice changes what is computed,
+only the order of FP32 sums.
 """
 from __future__ import annotations
 
@@ -15,15 +26,16 @@ from typing import Dict, Optional, Sequence, Tuple
 
 _CACHE: Dict[tuple, dict] = {}
 ENV_KINDS = (1, 2, 3, 4)
-SPLITS = (1, 2, 4, 8)
+SOLVE_TILES = ((2, 0), (1, 1), (1, 2), (1, 4), (1, 8))    # (solve_kernel, k1_split)
+FACTOR_CLUSTERS = (4, 8)
+KEYS = ("env_kernel", "solve_kernel", "k1_split", "factor_cluster")
 
 
 def _time_schedule(dims, ranks, n, ingest, sched, slices, steps) -> Optional[float]:
     import torch
     from .ttals import Stream, TTALSError
     try:
-        st = Stream(dims, ranks, ingest=ingest, n_streams=n, env_kernel=sched.get("env_kernel", 0),
-                    k1_split=sched.get("k1_split", 0))
+        st = Stream(dims, ranks, ingest=ingest, n_streams=n, **{k: sched.get(k, 0) for k in KEYS})
     except TTALSError:
         return None
     s = torch.cuda.current_stream()
@@ -59,21 +71,30 @@ def best_schedule(dims: Sequence[int], ranks: Sequence[int], n: int, ingest: str
     shape = (2, n) + tuple(int(v) for v in dims)
     base = torch.randn(shape, generator=g, device="cuda", dtype=torch.float32)
     slices = (base * 16 + 128).clamp(0, 255).round().to(dt)
-    results: Dict[Tuple[int, int], float] = {}
+    results: Dict[Tuple[int, int, int, int], float] = {}
+
+    def trial(e, sk, ks, fc):
+        key4 = (e, sk, ks, fc)
+        if key4 not in results:
+            ms = _time_schedule(dims, ranks, n, ingest, dict(zip(KEYS, key4)), slices, steps)
+            if ms is not None:
+                results[key4] = ms
+        return results.get(key4)
+
     for e in ENV_KINDS:
-        ms = _time_schedule(dims, ranks, n, ingest, {"env_kernel": e}, slices, steps)
-        if ms is not None:
-            results[(e, 0)] = ms
+        trial(e, 0, 0, 0)
     if not results:
         _CACHE[key] = {}
         return {}
     e_best = min(results, key=results.get)[0]
-    for k in SPLITS:
-        ms = _time_schedule(dims, ranks, n, ingest, {"env_kernel": e_best, "k1_split": k}, slices, steps)
-        if ms is not None:
-            results[(e_best, k)] = ms
-    (e, k) = min(results, key=results.get)
-    best = {"env_kernel": e, "k1_split": k, "ms_per_step": results[(e, k)],
-            "tried": {f"env{ee}_split{kk}": round(v, 4) for (ee, kk), v in sorted(results.items())}}
+    for sk, ks in SOLVE_TILES:
+        trial(e_best, sk, ks, 0)
+    _, sk_best, ks_best, _ = min(results, key=results.get)
+    for fc in FACTOR_CLUSTERS:
+        trial(e_best, sk_best, ks_best, fc)
+    best4 = min(results, key=results.get)
+    best = dict(zip(KEYS, best4))
+    best["ms_per_step"] = results[best4]
+    best["tried"] = {f"env{a}_solve{b}_split{c}_fc{d}": round(v, 4) for (a, b, c, d), v in sorted(results.items())}
     _CACHE[key] = best
     return best

@@ -55,6 +55,10 @@ def test_invalid_arguments_rejected_before_cuda(lib):
     assert lib.ttals_create(2, dims, ranks, ctypes.byref(cfg), ctypes.byref(h)) == 1   # env_kernel 5
     cfg = T.Config(2, 1, 0, 0, 0, 3, 0, 0)
     assert lib.ttals_create(2, dims, ranks, ctypes.byref(cfg), ctypes.byref(h)) == 1   # k1_split 3
+    cfg = T.Config(2, 1, 0, 0, 0, 0, 0, 0, 3, 0)
+    assert lib.ttals_create(2, dims, ranks, ctypes.byref(cfg), ctypes.byref(h)) == 1   # solve_kernel 3
+    cfg = T.Config(2, 1, 0, 0, 0, 0, 0, 0, 0, 6)
+    assert lib.ttals_create(2, dims, ranks, ctypes.byref(cfg), ctypes.byref(h)) == 1   # factor_cluster 6
     ranks = (ctypes.c_int64 * 2)(65, 65)
     dims = (ctypes.c_int64 * 2)(100, 100)
     assert lib.ttals_create(2, dims, ranks, None, ctypes.byref(h)) == 1      # rank above 64

@@ -187,3 +187,33 @@ def test_batch_16_video_streams_full_size():
         for t in range(T):
             rel = np.linalg.norm(batch[b][0][t] - xa[t]) / np.linalg.norm(xa[t])
             assert rel <= (1e-4 if t == 0 else 1e-3), (b, t, rel)
+
+
+@pytest.mark.parametrize("sched", [{"solve_kernel": 2, "factor_cluster": 4},
+                                   {"solve_kernel": 1, "k1_split": 2, "factor_cluster": 8},
+                                   {"env_kernel": 3, "solve_kernel": 2, "factor_cluster": 4},
+                                   {"env_kernel": 4, "solve_kernel": 1, "k1_split": 8, "factor_cluster": 4}])
+def test_batch_schedules_agree(sched):
+    """Every tile-shape schedule the autotuner may pick (solve kernel and split, environment
+    kernel, factor cluster) computes the same update as the library's default schedule:
+    only FP32 summation orders differ (first step within 1e-4, later ones within 1e-3)."""
+    torch = _torch()
+    from paper_2606_31061_b300.ttals import Stream
+    nb, T = 3, 4
+    ss = [_stream("video", {"dims": (96, 128, 3)}, b, T) for b in range(nb)]
+    dims, ranks = ss[0][0], ss[0][1]
+    base = _run_batch(torch, dims, ranks, [(s[2], s[3], s[4]) for s in ss])
+    bt = Stream(dims, ranks, ingest="f16", n_streams=nb, **sched)
+    for b, s in enumerate(ss):
+        bt.select(b)
+        bt.set_cores(s[3], s[4])
+    out = torch.empty(tuple(dims), dtype=torch.float64, device="cuda")
+    for t in range(T):
+        bt.push_batch(torch.from_numpy(np.stack([s[2][t] for s in ss])).view(torch.float16).cuda())
+        for b in range(nb):
+            bt.select(b)
+            bt.reconstruct(out, "f64")
+            x = out.cpu().numpy()
+            rel = np.linalg.norm(x - base[b][0][t]) / np.linalg.norm(base[b][0][t])
+            assert rel <= (1e-4 if t == 0 else 1e-3), (sched, b, t, rel)
+    bt.close()
