@@ -60,7 +60,8 @@ constexpr int kSMs = 148;
 
 inline long long cdiv(long long a, long long b) { return (a + b - 1) / b; }
 
-// split-K choice for the generic GEMM: enough CTAs for ~2 waves on 148 SMs
+// split-K choice for the generic GEMM: enough CTAs for ~2 waves on 148 SMs, at most
+// max_split splits (the split partials are summed afterwards, per output element)
 struct GemmShape {
   int M, N;
   long long K;
@@ -69,7 +70,7 @@ struct GemmShape {
   dim3 grid;
 };
 
-GemmShape plan_gemm(int M, int N, long long K, bool allow_split) {
+GemmShape plan_gemm(int M, int N, long long K, bool allow_split, int max_split = 64) {
   GemmShape g;
   g.M = M;
   g.N = N;
@@ -77,7 +78,7 @@ GemmShape plan_gemm(int M, int N, long long K, bool allow_split) {
   const long long tiles = cdiv(M, GB_M) * cdiv(N, GB_N);
   long long ns = allow_split ? std::max<long long>(1, cdiv(2 * kSMs, tiles)) : 1;
   ns = std::min<long long>(ns, std::max<long long>(1, cdiv(K, GB_K)));
-  ns = std::min<long long>(ns, 64);
+  ns = std::min<long long>(ns, max_split);
   long long kc = cdiv(cdiv(K, ns), GB_K) * GB_K;
   if (kc < GB_K) kc = GB_K;
   g.kchunk = kc;
@@ -312,7 +313,7 @@ struct Impl final : ttals_stream {
   TC* part = nullptr;                  // split-K partials
   TC* Y = nullptr;                     // reduced local-solve matrix of a level
   TC* Qa = nullptr;                    // first-pass orthogonal factor
-  double* Wpart = nullptr;
+  TC* Wpart = nullptr;            // per-CTA Gram partials (accumulation type TG = TC)
   double* T64 = nullptr;
   float* T32 = nullptr;
   double* sumsq = nullptr;
@@ -374,11 +375,15 @@ struct Impl final : ttals_stream {
   int rows(int k) const { return (int)(full[k - 1] * dims[k - 1]); }  // r_{k-1} I_k
   int rk(int k) const { return (int)full[k]; }
 
+  // FP32 state: up to 256 k-splits (a long contraction with few output tiles, e.g. 32 x 32^3
+  // slices, then keeps every CTA to a few K stages; the partials are summed as float-float
+  // pairs); FP64 state: 64 (its partials are summed in FP64)
+  static constexpr int kMaxSplit = std::is_same<TC, float>::value ? 256 : 64;
   GemmShape plan_solve(int k) const {      // Y = E_k B^_k^T
-    return plan_gemm(rows(k), rk(k), rest[k], true);
+    return plan_gemm(rows(k), rk(k), rest[k], true, kMaxSplit);
   }
   GemmShape plan_env(int k) const {        // E_{k+1}^T = E_k^T Q_k
-    return plan_gemm((int)rest[k], rk(k), rows(k), true);
+    return plan_gemm((int)rest[k], rk(k), rows(k), true, kMaxSplit);
   }
   int gram_blocks(long long nrows) const { return (int)std::min<long long>(64, cdiv(nrows, 16)); }
 
@@ -436,7 +441,7 @@ struct Impl final : ttals_stream {
     TT_TRY(dalloc(&ctl, (size_t)nbatch));
     TT_CUDA(cudaMemset(ctl, 0, sizeof(Ctl) * nbatch));
     ctl_base = ctl;
-    TT_CUDA(cudaFuncSetAttribute(k_factor, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024));
+    TT_CUDA(cudaFuncSetAttribute(k_factor<TC>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024));
     TT_CUDA(cudaFuncSetAttribute(fast::k_chol64_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024));
     TT_TRY(setup_fast());
     return TTALS_OK;
@@ -944,7 +949,7 @@ struct Impl final : ttals_stream {
       k_gram<TC, TC, TG><<<nblk, GRAM_THREADS, gsm, s>>>(src, pass == 0 ? nsplit : 1, n * r, n, r,
                                                           (pass == 0 && !src0) ? Y : nullptr, Wpart, rpb, ctl);
       TT_CUDA(cudaGetLastError());
-      k_factor<<<1, FACT_THREADS, fsm, s>>>(Wpart, nblk, r, pass == 0 ? 0 : 1, T64, T32, ctl, slot,
+      k_factor<TC><<<1, FACT_THREADS, fsm, s>>>(Wpart, nblk, r, pass == 0 ? 0 : 1, T64, T32, ctl, slot,
                                              sumsq, sum_n, (first && pass == 0) ? 1 : 0);
       TT_CUDA(cudaGetLastError());
       k_apply<TC><<<ablk, APPLY_THREADS, asm_, s>>>(pass == 0 ? Y : Qa, n, r, pass == 0 ? 0 : 1, T64, T32,

@@ -254,7 +254,10 @@ __global__ void __launch_bounds__(G_THREADS) k_gemm(
 // Gram partials of a tall matrix.  Rows [b*rpb, (b+1)*rpb) of
 //   Y = sum_{s < nsplit} P[s]     (P[s] is rows x r, element (i,j) at i*r + j)
 // are formed (fixed summation order), optionally written to Yout, and
-//   Wpart[b] = Y_b^T Y_b  (r x r, upper triangle; accumulated in TG, stored FP64).
+//   Wpart[b] = Y_b^T Y_b  (r x r, upper triangle; accumulated and stored in TG).
+// FP32 partials P are summed as float-float pairs (TwoSum on the FP32 pipe: this part's FP64
+// unit issues one warp instruction per ~64 cycles, which made FP64 sums of many partials the
+// kernel's cost); FP64 partials in FP64.
 // --------------------------------------------------------------------------
 constexpr int GRAM_THREADS = 256;
 constexpr int GRAM_CHUNK = 32;   // rows staged in shared memory at a time
@@ -262,7 +265,7 @@ constexpr int GRAM_CHUNK = 32;   // rows staged in shared memory at a time
 template <typename TP, typename TY, typename TG>
 __global__ void __launch_bounds__(GRAM_THREADS) k_gram(
     const TP* __restrict__ P, int nsplit, long long sstride, long long rows, int r,
-    TY* __restrict__ Yout, double* __restrict__ Wpart, long long rpb, const Ctl* __restrict__ ctl) {
+    TY* __restrict__ Yout, TG* __restrict__ Wpart, long long rpb, const Ctl* __restrict__ ctl) {
   if (ctl && ctl->skip) return;
   extern __shared__ unsigned char smem_raw[];
   TG* ys = reinterpret_cast<TG*>(smem_raw);               // GRAM_CHUNK x r
@@ -278,7 +281,18 @@ __global__ void __launch_bounds__(GRAM_THREADS) k_gram(
     for (int e = threadIdx.x; e < nr * r; e += blockDim.x) {
       const long long gi = (c0 + e / r) * r + e % r;
       double v = 0.0;
-      for (int s = 0; s < nsplit; ++s) v += Cvt<TP>::d(P[(long long)s * sstride + gi]);
+      if constexpr (std::is_same<TP, float>::value) {
+        float h = 0.f, l = 0.f;
+        for (int s = 0; s < nsplit; ++s) {
+          const float p = P[(long long)s * sstride + gi];
+          const float t = h + p, bb = t - h;
+          l += (h - (t - bb)) + (p - bb);
+          h = t;
+        }
+        v = (double)h + (double)l;
+      } else {
+        for (int s = 0; s < nsplit; ++s) v += Cvt<TP>::d(P[(long long)s * sstride + gi]);
+      }
       const TY yv = from_acc<TY>(v);
       if (Yout) Yout[gi] = yv;
       ys[e] = (TG)Cvt<TY>::d(yv);
@@ -296,11 +310,11 @@ __global__ void __launch_bounds__(GRAM_THREADS) k_gram(
     }
     __syncthreads();
   }
-  double* W = Wpart + (long long)blockIdx.x * npair;
+  TG* W = Wpart + (long long)blockIdx.x * npair;
 #pragma unroll
   for (int q = 0; q < 16; ++q) {
     const int e = threadIdx.x + q * GRAM_THREADS;
-    if (e < npair) W[e] = (double)acc[q];
+    if (e < npair) W[e] = acc[q];
   }
 }
 
@@ -322,8 +336,9 @@ __global__ void __launch_bounds__(GRAM_THREADS) k_gram(
 constexpr int FACT_THREADS = 1024;
 constexpr int kMaxRank = 64;
 
+template <typename TW>
 __global__ void __launch_bounds__(FACT_THREADS) k_factor(
-    const double* __restrict__ Wpart, int nblk, int r, int mode, double* __restrict__ T64,
+    const TW* __restrict__ Wpart, int nblk, int r, int mode, double* __restrict__ T64,
     float* __restrict__ T32, Ctl* __restrict__ ctl, int slot, const double* __restrict__ sumsq,
     int nsum, int first) {
   extern __shared__ unsigned char smem_raw[];
@@ -351,7 +366,19 @@ __global__ void __launch_bounds__(FACT_THREADS) k_factor(
     const int i = e / r, j = e % r;
     const int ii = i <= j ? i : j, jj = i <= j ? j : i;     // read the upper triangle
     double s = 0.0;
-    for (int b = 0; b < nblk; ++b) s += Wpart[(long long)b * rr + ii * r + jj];
+    if constexpr (std::is_same<TW, float>::value) {
+      // float partials: float-float sum (TwoSum), one conversion at the end
+      float h = 0.f, l = 0.f;
+      for (int b = 0; b < nblk; ++b) {
+        const float p = Wpart[(long long)b * rr + ii * r + jj];
+        const float t = h + p, bb = t - h;
+        l += (h - (t - bb)) + (p - bb);
+        h = t;
+      }
+      s = (double)h + (double)l;
+    } else {
+      for (int b = 0; b < nblk; ++b) s += Wpart[(long long)b * rr + ii * r + jj];
+    }
     W[e] = s;
     if (!isfinite(s)) bad = 1;
   }
@@ -571,7 +598,11 @@ __global__ void __launch_bounds__(APPLY_THREADS) k_apply(
 
 // --------------------------------------------------------------------------
 // out[a][j] = sum_s P[s][j][a]   (transpose-reduce of split partials; r x rest)
-// plus per-CTA partials of sum(out^2) when ccpart != nullptr.
+// plus per-CTA partials of sum(out^2) when ccpart != nullptr.  Tiles of 32 values of j
+// (all r values of a) are read along P's rows and written along out's rows through shared
+// memory, so that both sides are coalesced.  FP32 partials are summed as float-float pairs
+// (TwoSum, and TwoProd for the squares) on the FP32 pipe, FP64 ones in FP64; each in split
+// order.
 // --------------------------------------------------------------------------
 constexpr int RED_THREADS = 256;
 
@@ -581,20 +612,48 @@ __global__ void __launch_bounds__(RED_THREADS) k_reduce_t(
     TC* __restrict__ out, double* __restrict__ ccpart, const Ctl* __restrict__ ctl) {
   if (ctl && ctl->skip) return;
   __shared__ double red[32];
-  const long long total = rest * r;
+  __shared__ TC tile[32 * 65];          // 32 values of j x r (<= 64) values of a, rows padded
+  const int ld = r + 1;
   double ss = 0.0;
-  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
-       e += (long long)gridDim.x * blockDim.x) {
-    const long long j = e / r;
-    const int a = (int)(e % r);
-    double v = 0.0;
-    for (int s = 0; s < nsplit; ++s) v += Cvt<TC>::d(P[(long long)s * sstride + e]);
-    const TC o = from_acc<TC>(v);
-    out[(long long)a * rest + j] = o;
-    const double od = Cvt<TC>::d(o);
-    ss += od * od;
+  float sh = 0.f, sl = 0.f;             // float-float sum of squares (FP32 partials)
+  const long long ntile = (rest + 31) / 32;
+  for (long long t = blockIdx.x; t < ntile; t += gridDim.x) {
+    const long long j0 = t * 32;
+    const int nj = (int)(rest - j0 < 32 ? rest - j0 : 32);
+    for (int q = threadIdx.x; q < nj * r; q += blockDim.x) {
+      const long long e = j0 * r + q;
+      TC o;
+      if constexpr (std::is_same<TC, float>::value) {
+        float h = 0.f, l = 0.f;
+        for (int s = 0; s < nsplit; ++s) {
+          const float p = P[(long long)s * sstride + e];
+          const float u = h + p, bb = u - h;
+          l += (h - (u - bb)) + (p - bb);
+          h = u;
+        }
+        o = h + l;
+        const float pr = o * o, pe = fmaf(o, o, -pr);
+        const float u = sh + pr, bb = u - sh;
+        sl += ((sh - (u - bb)) + (pr - bb)) + pe;
+        sh = u;
+      } else {
+        double v = 0.0;
+        for (int s = 0; s < nsplit; ++s) v += Cvt<TC>::d(P[(long long)s * sstride + e]);
+        o = from_acc<TC>(v);
+        const double od = Cvt<TC>::d(o);
+        ss += od * od;
+      }
+      tile[(q / r) * ld + q % r] = o;
+    }
+    __syncthreads();
+    for (int q = threadIdx.x; q < r * 32; q += blockDim.x) {
+      const int a = q / 32, jl = q % 32;
+      if (jl < nj) out[(long long)a * rest + j0 + jl] = tile[jl * ld + a];
+    }
+    __syncthreads();
   }
   if (ccpart) {
+    if constexpr (std::is_same<TC, float>::value) ss = (double)sh + (double)sl;
     const double tot = block_sum(ss, red);
     if (threadIdx.x == 0) ccpart[blockIdx.x] = tot;
   }
@@ -606,9 +665,20 @@ __global__ void k_reduce_rows(const TC* __restrict__ P, int nsplit, long long n,
                               const Ctl* __restrict__ ctl) {
   if (ctl && ctl->skip) return;
   for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
-    double v = 0.0;
-    for (int q = 0; q < nsplit; ++q) v += Cvt<TC>::d(P[(long long)q * n + e]);
-    out[e] = from_acc<TC>(v);
+    if constexpr (std::is_same<TC, float>::value) {
+      float h = 0.f, l = 0.f;           // float-float (TwoSum), as in k_reduce_t
+      for (int q = 0; q < nsplit; ++q) {
+        const float p = P[(long long)q * n + e];
+        const float u = h + p, bb = u - h;
+        l += (h - (u - bb)) + (p - bb);
+        h = u;
+      }
+      out[e] = h + l;
+    } else {
+      double v = 0.0;
+      for (int q = 0; q < nsplit; ++q) v += Cvt<TC>::d(P[(long long)q * n + e]);
+      out[e] = from_acc<TC>(v);
+    }
   }
 }
 
