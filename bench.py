@@ -132,20 +132,28 @@ def to_device(pool_np, ingest):
     return t.cuda()
 
 
+# the sources of the fused kernels whose DRAM traffic profiles/traffic.json records
+TRAFFIC_SOURCES = ("ttals_fast.cuh", "ttals_r64.cuh")
+
+
+def traffic_sha256():
+    import hashlib
+    h = hashlib.sha256()
+    src = os.path.join(ROOT, "paper_2606_31061_b300", "csrc")
+    for name in TRAFFIC_SOURCES:
+        h.update(open(os.path.join(src, name), "rb").read())
+    return h.hexdigest()
+
+
 def traffic_record(kernel, sub=None):
-    """DRAM bytes per launch from a committed ncu capture, if the kernel sources are unchanged
-    (`sub`: the kernel within a batched record)."""
+    """DRAM bytes per launch from a committed ncu capture, if the fused kernels' sources are
+    unchanged (`sub`: the kernel within a batched record)."""
     try:
-        import hashlib
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
             rec = json.load(f)
-        h = hashlib.sha256()
-        src = os.path.join(ROOT, "paper_2606_31061_b300", "csrc")
-        for name in sorted(os.listdir(src)):
-            if name.endswith((".cu", ".cuh")):
-                h.update(open(os.path.join(src, name), "rb").read())
+        digest = traffic_sha256()
         r = rec.get(kernel)
-        if r and r.get("src_sha256") == h.hexdigest():
+        if r and r.get("src_sha256") == digest:
             return r["kernel_bytes_per_launch"].get(sub) if sub else r.get("bytes_per_launch")
     except Exception:
         pass
