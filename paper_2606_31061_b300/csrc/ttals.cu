@@ -818,7 +818,9 @@ struct Impl final : ttals_stream {
       a2.ch_shift_old = fShiftb + par;
       a2.is_half = std::is_same<TX, __half>::value ? 1 : 0;
       a2.w2_parts = kbc;
-      std::memcpy(a2.zmap, zact, sizeof(zact));
+      // the environment kernel takes the stepping streams in the reverse of the solve kernel's
+      // order: the slices the solve read last (up to the L2's size) are then read again from L2
+      for (int z = 0; z < n_act; ++z) a2.zmap[z] = zact[n_act - 1 - z];
       at[0].val.clusterDim.y = (unsigned)k2_nq;
       cudaLaunchConfig_t c2{};
       c2.gridDim = dim3((unsigned)k2_cols, (unsigned)k2_nq, (unsigned)n_act);
