@@ -60,8 +60,9 @@ constexpr int kSMs = 148;
 
 inline long long cdiv(long long a, long long b) { return (a + b - 1) / b; }
 
-// split-K choice for the generic GEMM: enough CTAs for ~2 waves on 148 SMs, at most
-// max_split splits (the split partials are summed afterwards, per output element)
+// split-K choice for the generic GEMM: about target_ctas CTAs (default: two waves on 148
+// SMs), at most max_split splits of at least min_kchunk (the split partials are summed
+// afterwards, per output element)
 struct GemmShape {
   int M, N;
   long long K;
@@ -70,14 +71,15 @@ struct GemmShape {
   dim3 grid;
 };
 
-GemmShape plan_gemm(int M, int N, long long K, bool allow_split, int max_split = 64) {
+GemmShape plan_gemm(int M, int N, long long K, bool allow_split, int max_split = 64, int target_ctas = 2 * kSMs,
+                    long long min_kchunk = GB_K) {
   GemmShape g;
   g.M = M;
   g.N = N;
   g.K = K;
   const long long tiles = cdiv(M, GB_M) * cdiv(N, GB_N);
-  long long ns = allow_split ? std::max<long long>(1, cdiv(2 * kSMs, tiles)) : 1;
-  ns = std::min<long long>(ns, std::max<long long>(1, cdiv(K, GB_K)));
+  long long ns = allow_split ? std::max<long long>(1, cdiv(target_ctas, tiles)) : 1;
+  ns = std::min<long long>(ns, std::max<long long>(1, cdiv(K, min_kchunk)));
   ns = std::min<long long>(ns, max_split);
   long long kc = cdiv(cdiv(K, ns), GB_K) * GB_K;
   if (kc < GB_K) kc = GB_K;
@@ -375,15 +377,20 @@ struct Impl final : ttals_stream {
   int rows(int k) const { return (int)(full[k - 1] * dims[k - 1]); }  // r_{k-1} I_k
   int rk(int k) const { return (int)full[k]; }
 
-  // FP32 state: up to 256 k-splits (a long contraction with few output tiles, e.g. 32 x 32^3
-  // slices, then keeps every CTA to a few K stages; the partials are summed as float-float
-  // pairs); FP64 state: 64 (its partials are summed in FP64)
-  static constexpr int kMaxSplit = std::is_same<TC, float>::value ? 256 : 64;
+  // FP32 state: splits for about 8 resident CTAs per SM (the K loop waits on one global load
+  // per 32-wide step, so occupancy is what hides its latency), at least 4 K steps each, up to
+  // 1024 (a long contraction with few output tiles: 32 x 32^3 or 30 x 30^5 slices; the
+  // partials are summed as float-float pairs); FP64 state: two waves, up to 64 splits (its
+  // partials are summed in FP64)
+  static constexpr bool kF32State = std::is_same<TC, float>::value;
+  static constexpr int kMaxSplit = kF32State ? 1024 : 64;
+  static constexpr int kTargetCtas = kF32State ? 8 * kSMs : 2 * kSMs;
+  static constexpr long long kMinChunk = kF32State ? 4 * GB_K : GB_K;
   GemmShape plan_solve(int k) const {      // Y = E_k B^_k^T
-    return plan_gemm(rows(k), rk(k), rest[k], true, kMaxSplit);
+    return plan_gemm(rows(k), rk(k), rest[k], true, kMaxSplit, kTargetCtas, kMinChunk);
   }
   GemmShape plan_env(int k) const {        // E_{k+1}^T = E_k^T Q_k
-    return plan_gemm((int)rest[k], rk(k), rows(k), true, kMaxSplit);
+    return plan_gemm((int)rest[k], rk(k), rows(k), true, kMaxSplit, kTargetCtas, kMinChunk);
   }
   int gram_blocks(long long nrows) const { return (int)std::min<long long>(64, cdiv(nrows, 16)); }
 
