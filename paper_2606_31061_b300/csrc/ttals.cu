@@ -925,13 +925,31 @@ struct Impl final : ttals_stream {
   }
 
   // ---- launch helpers --------------------------------------------------------
+  // a generic-path kernel with programmatic dependent launch (each such kernel waits for its
+  // predecessor at entry: gen_pdl_start), unless profiling or TTALS_NO_PDL
+  template <typename... KArgs, typename... Args>
+  ttals_status launch_gen(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                          Args&&... args) {
+    cudaLaunchConfig_t c{};
+    c.gridDim = grid;
+    c.blockDim = block;
+    c.dynamicSmemBytes = smem;
+    c.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = (profiling || no_pdl) ? 0 : 1;
+    c.attrs = at;
+    c.numAttrs = 1;
+    TT_CUDA(cudaLaunchKernelEx(&c, kern, std::forward<Args>(args)...));
+    return TTALS_OK;
+  }
+
   template <typename TA, typename TB, typename TACC, typename TD, bool AK, bool BK>
   ttals_status gemm(const GemmShape& g, const TA* A, long long lda, const TB* B, long long ldb, TD* D,
                     long long sdm, long long sdn, long long sstride, double* ss,
                     const double* bzero, const Ctl* chk, Ctl* reset, cudaStream_t s) {
-    k_gemm<TA, TB, TACC, TD, AK, BK><<<g.grid, G_THREADS, 0, s>>>(
-        A, lda, B, ldb, D, sdm, sdn, sstride, g.M, g.N, g.K, g.kchunk, ss, bzero, chk, reset);
-    TT_CUDA(cudaGetLastError());
+    TT_TRY(launch_gen(k_gemm<TA, TB, TACC, TD, AK, BK>, g.grid, dim3(G_THREADS), 0, s, A, lda, B, ldb, D, sdm,
+                      sdn, sstride, g.M, g.N, g.K, g.kchunk, ss, bzero, chk, reset));
     ++nlaunch;
     return TTALS_OK;
   }
@@ -955,15 +973,15 @@ struct Impl final : ttals_stream {
       // already in Y) and leaves the reduced solve in Y
       const TC* src = pass == 0 ? (src0 ? src0 : (const TC*)part) : (const TC*)Qa;
       TC* dst = (pass + 1 == qr_passes) ? qout : Qa;
-      k_gram<TC, TC, TG><<<nblk, GRAM_THREADS, gsm, s>>>(src, pass == 0 ? nsplit : 1, n * r, n, r,
-                                                          (pass == 0 && !src0) ? Y : nullptr, Wpart, rpb, ctl);
-      TT_CUDA(cudaGetLastError());
-      k_factor<TC><<<1, FACT_THREADS, fsm, s>>>(Wpart, nblk, r, pass == 0 ? 0 : 1, T64, T32, ctl, slot,
-                                             sumsq, sum_n, (first && pass == 0) ? 1 : 0);
-      TT_CUDA(cudaGetLastError());
-      k_apply<TC><<<ablk, APPLY_THREADS, asm_, s>>>(pass == 0 ? Y : Qa, n, r, pass == 0 ? 0 : 1, T64, T32,
-                                                     dst, ctl, slot, hh);
-      TT_CUDA(cudaGetLastError());
+      TT_TRY(launch_gen(k_gram<TC, TC, TG>, dim3(nblk), dim3(GRAM_THREADS), gsm, s, src, pass == 0 ? nsplit : 1,
+                        (long long)(n * r), (long long)n, r, (pass == 0 && !src0) ? Y : (TC*)nullptr, Wpart, (long long)rpb,
+                        (const Ctl*)ctl));
+      TT_TRY(launch_gen(k_factor<TC>, dim3(1), dim3(FACT_THREADS), fsm, s, (const TC*)Wpart, nblk, r,
+                        pass == 0 ? 0 : 1, T64, T32, ctl, slot, (const double*)sumsq, sum_n,
+                        (first && pass == 0) ? 1 : 0));
+      TT_TRY(launch_gen(k_apply<TC>, dim3(ablk), dim3(APPLY_THREADS), asm_, s, pass == 0 ? (const TC*)Y : (const TC*)Qa,
+                        (long long)n, r, pass == 0 ? 0 : 1, (const double*)T64, (const float*)T32, dst,
+                        (const Ctl*)ctl, slot, hh));
       nlaunch += 3;
     }
     return TTALS_OK;
@@ -998,10 +1016,9 @@ struct Impl final : ttals_stream {
 
     if (kstar == 1) {   // r_1 >= I_2...I_{n-1}: x^_t = X_t
       const int nb = (int)std::min<long long>(cdiv(rest[0], 256), 2 * kSMs);
-      k_copy_slice<TX, TC><<<nb, 256, 0, s>>>(X, rest[0], C[np], ccpart, ctl);
-      TT_CUDA(cudaGetLastError());
-      k_commit<<<1, 256, 0, s>>>(ctl, ccpart, nb, ccpart, nb, rl);
-      TT_CUDA(cudaGetLastError());
+      TT_TRY(launch_gen(k_copy_slice<TX, TC>, dim3(nb), dim3(256), 0, s, X, (long long)rest[0], C[np], ccpart, ctl));
+      TT_TRY(launch_gen(k_commit, dim3(1), dim3(256), 0, s, ctl, (const double*)ccpart, nb, (const double*)ccpart, nb,
+                        rl));
       nlaunch += 2;
       par = np;
       return TTALS_OK;
@@ -1046,14 +1063,14 @@ struct Impl final : ttals_stream {
       }
       TC* eout = last_level ? C[np] : E[k + 1];
       const int nb = (int)std::min<long long>(cdiv(rest[k] * rk(k), RED_THREADS), 4 * kSMs);
-      k_reduce_t<TC><<<nb, RED_THREADS, 0, s>>>(part, ge.nsplit, (long long)ge.M * ge.N, rest[k], rk(k), eout,
-                                                last_level ? ccpart : nullptr, ctl);
-      TT_CUDA(cudaGetLastError());
+      TT_TRY(launch_gen(k_reduce_t<TC>, dim3(nb), dim3(RED_THREADS), 0, s, (const TC*)part, ge.nsplit,
+                        (long long)ge.M * ge.N, (long long)rest[k], rk(k), eout,
+                        last_level ? ccpart : (double*)nullptr, (const Ctl*)ctl));
       ++nlaunch;
       if (last_level) ncc = nb;
     }
-    k_commit<<<1, 256, 0, s>>>(ctl, ccpart, ncc, nullptr, 0, rl);
-    TT_CUDA(cudaGetLastError());
+    TT_TRY(launch_gen(k_commit, dim3(1), dim3(256), 0, s, ctl, (const double*)ccpart, ncc, (const double*)nullptr, 0,
+                      rl));
     ++nlaunch;
     par = np;
     return TTALS_OK;

@@ -53,6 +53,15 @@ __device__ unsigned long long g_ttals_cta[1024 * 4];
   } while (0)
 #endif
 
+// Programmatic dependent launch on the generic path: a kernel launched with the
+// programmatic-serialisation attribute may start while its predecessor runs; it waits here
+// for the predecessor's completion (and memory) before touching anything the step writes,
+// and lets its own successor be scheduled at once.  Without the attribute both are no-ops.
+__device__ __forceinline__ void gen_pdl_start() {
+  asm volatile("griddepcontrol.wait;\n" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
+}
+
 // --------------------------------------------------------------------------
 // control block shared by the kernels of one stream (device memory)
 // --------------------------------------------------------------------------
@@ -158,6 +167,7 @@ __global__ void __launch_bounds__(G_THREADS) k_gemm(
     TD* __restrict__ D, long long sdm, long long sdn, long long split_stride,
     int M, int N, long long K, long long kchunk, double* __restrict__ sumsq,
     const double* __restrict__ b_zero_flag, const Ctl* __restrict__ ctl, Ctl* __restrict__ reset) {
+  gen_pdl_start();
   if (ctl && ctl->skip) return;
   if (reset && blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && threadIdx.x == 0) {
     reset->skip = 0;
@@ -266,6 +276,7 @@ template <typename TP, typename TY, typename TG>
 __global__ void __launch_bounds__(GRAM_THREADS) k_gram(
     const TP* __restrict__ P, int nsplit, long long sstride, long long rows, int r,
     TY* __restrict__ Yout, TG* __restrict__ Wpart, long long rpb, const Ctl* __restrict__ ctl) {
+  gen_pdl_start();
   if (ctl && ctl->skip) return;
   extern __shared__ unsigned char smem_raw[];
   TG* ys = reinterpret_cast<TG*>(smem_raw);               // GRAM_CHUNK x r
@@ -341,6 +352,7 @@ __global__ void __launch_bounds__(FACT_THREADS) k_factor(
     const TW* __restrict__ Wpart, int nblk, int r, int mode, double* __restrict__ T64,
     float* __restrict__ T32, Ctl* __restrict__ ctl, int slot, const double* __restrict__ sumsq,
     int nsum, int first) {
+  gen_pdl_start();
   extern __shared__ unsigned char smem_raw[];
   double* W = reinterpret_cast<double*>(smem_raw);                 // r*r
   double* dsc = W + r * r;                                         // r
@@ -562,6 +574,7 @@ __global__ void __launch_bounds__(APPLY_THREADS) k_apply(
     const TQ* __restrict__ Y, long long rows, int r, int mode, const double* __restrict__ T64,
     const float* __restrict__ T32, TQ* __restrict__ Qout, const Ctl* __restrict__ ctl, int slot,
     double* __restrict__ hh_work) {
+  gen_pdl_start();
   if (ctl->skip) return;
   if (ctl->fallback[slot]) {
     if (blockIdx.x == 0) {
@@ -610,6 +623,7 @@ template <typename TC>
 __global__ void __launch_bounds__(RED_THREADS) k_reduce_t(
     const TC* __restrict__ P, int nsplit, long long sstride, long long rest, int r,
     TC* __restrict__ out, double* __restrict__ ccpart, const Ctl* __restrict__ ctl) {
+  gen_pdl_start();
   if (ctl && ctl->skip) return;
   __shared__ double red[32];
   __shared__ TC tile[32 * 65];          // 32 values of j x r (<= 64) values of a, rows padded
@@ -715,6 +729,7 @@ __global__ void k_dot_part(const TC* __restrict__ a, const TC* __restrict__ b, l
 template <typename TX, typename TC>
 __global__ void k_copy_slice(const TX* __restrict__ X, long long n, TC* __restrict__ C,
                              double* __restrict__ ccpart, Ctl* __restrict__ reset) {
+  gen_pdl_start();
   if (reset && blockIdx.x == 0 && threadIdx.x == 0) {
     reset->skip = 0;
     for (int i = 0; i < kMaxSlots; ++i) reset->fallback[i] = 0;
@@ -744,6 +759,7 @@ struct CopyList {
 
 __global__ void k_commit(Ctl* __restrict__ ctl, const double* __restrict__ ccpart, int ncc,
                          const double* __restrict__ xxpart, int nxx, CopyList restore) {
+  gen_pdl_start();
   __shared__ double red[32];
   if (xxpart) {        // k* = 1: ||x||^2 comes from the copy kernel
     double v = 0.0;
