@@ -344,7 +344,7 @@ __global__ void __launch_bounds__(GRAM_THREADS) k_gram(
 // When `first` is set it also sums the per-CTA ||x||^2 partials into ctl->xx and
 // flags non-finite data (the step is then skipped, ENONFINITE latched).
 // --------------------------------------------------------------------------
-constexpr int FACT_THREADS = 1024;
+constexpr int FACT_THREADS = 256;
 constexpr int kMaxRank = 64;
 
 template <typename TW>
@@ -434,32 +434,48 @@ __global__ void __launch_bounds__(FACT_THREADS) k_factor(
     S[i * LD + j] = (float)(W[e] * dsc[i] * dsc[j]);
   }
   __syncthreads();
+  // right-looking elimination with one barrier per pivot: row j stays unscaled (d_j times the
+  // unit factor's row) until every pivot is done; the pivot's reciprocal is the hardware
+  // approximation refined by one Newton step (about 1e-7 relative)
+  __shared__ float rs[kMaxRank];                // 1 / sqrt(pivot j) = 1 / R_jj
   for (int j = 0; j < r; ++j) {
     const float piv = S[j * LD + j];
     if (!(piv > 1e-4f)) {            // uniform: every thread reads the same value
       if (tid == 0) ctl->fallback[slot] = 1;
       return;
     }
-    const float inv = 1.0f / piv;
-    // trailing update with the unscaled row j
-    for (int e = tid; e < rr; e += blockDim.x) {
-      const int i = e / r, k = e % r;
-      if (i > j && k >= i) S[i * LD + k] -= S[j * LD + i] * S[j * LD + k] * inv;
+    float inv;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(inv) : "f"(piv));
+    inv = inv * fmaf(-piv, inv, 2.0f);
+    if (tid == 0) rs[j] = rsqrtf(piv);
+    const int nt = r - j - 1;
+    for (int e = tid; e < nt * nt; e += blockDim.x) {
+      const int i = j + 1 + e / nt, k = j + 1 + e % nt;
+      if (k >= i) S[i * LD + k] = fmaf(-S[j * LD + i] * inv, S[j * LD + k], S[i * LD + k]);
     }
     __syncthreads();
-    if (tid < r && tid >= j) S[j * LD + tid] *= rsqrtf(piv);
-    __syncthreads();
   }
-  // Tinv = S^{-1} (upper triangular), column-parallel back substitution, into W (as float)
+  // R = the rows scaled by 1 / sqrt(pivot): R^T R = D W D
+  for (int e = tid; e < rr; e += blockDim.x) {
+    const int j = e / r, k = e % r;
+    if (k >= j) S[j * LD + k] *= rs[j];
+  }
+  __syncthreads();
+  // Tinv = R^{-1} (upper triangular), column-parallel back substitution, into W (as float)
   float* Ti = reinterpret_cast<float*>(W);   // r x r, reuse
   if (tid < r) {
     const int c = tid;
     for (int i = 0; i < r; ++i) Ti[i * r + c] = 0.f;
-    Ti[c * r + c] = 1.0f / S[c * LD + c];
+    Ti[c * r + c] = rs[c];
     for (int i = c - 1; i >= 0; --i) {
-      float s = 0.f;
-      for (int k = i + 1; k <= c; ++k) s = fmaf(S[i * LD + k], Ti[k * r + c], s);
-      Ti[i * r + c] = -s / S[i * LD + i];
+      float s0 = 0.f, s1 = 0.f;
+      int k = i + 1;
+      for (; k + 1 <= c; k += 2) {
+        s0 = fmaf(S[i * LD + k], Ti[k * r + c], s0);
+        s1 = fmaf(S[i * LD + k + 1], Ti[(k + 1) * r + c], s1);
+      }
+      if (k <= c) s0 = fmaf(S[i * LD + k], Ti[k * r + c], s0);
+      Ti[i * r + c] = -(s0 + s1) * rs[i];
     }
   }
   __syncthreads();
