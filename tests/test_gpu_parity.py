@@ -375,3 +375,31 @@ def test_fused_ill_conditioned_local_solves(factor):
         re_o = O.stream_relative_error(xs, xo)
         assert st.step() == 10
         assert abs(np.sqrt(s[3] / s[2]) - re_o) <= 1e-3, (name, kw, factor, np.sqrt(s[3] / s[2]), re_o)
+
+
+@pytest.mark.parametrize("name,kw,ingest", [("sensor", {"dims": (12, 12, 12, 16), "ranks": (6, 12, 12, 6)}, "f32"),
+                                            ("video", {"dims": (96, 128, 3)}, "f16")])
+def test_programmatic_launch_bitwise(monkeypatch, name, kw, ingest):
+    """Steps chained by programmatic dependent launch (each kernel may start while its
+    predecessor runs and waits for it at entry) give bitwise the results of plain stream
+    ordering (TTALS_NO_PDL=1, read when a stream is created): on the generic path (k* = 3)
+    and on the fused path, with eight steps enqueued back to back before any read."""
+    torch = _torch()
+    from paper_2606_31061_b300.ttals import Stream
+    sp = synth.make_stream(name, seed=77, **kw)
+    r = O.clamp_ranks(sp.dims, sp.ranks)
+    cores, g = synth.init_cores(sp.dims, r, seed=8)
+    frames = [_upload(x, ingest)[0] for x in sp.take(8)]
+    res = []
+    for flag in ("0", "1"):
+        monkeypatch.setenv("TTALS_NO_PDL", flag)
+        st = Stream(sp.dims, sp.ranks, ingest=ingest)
+        st.set_cores(cores, g)
+        for x in frames:
+            st.push(x)
+        out = torch.empty(tuple(sp.dims), dtype=torch.float64, device="cuda")
+        st.reconstruct(out, "f64")
+        res.append((out.cpu().numpy().copy(), np.array(st.stats())))
+        st.close()
+    assert np.array_equal(res[0][0], res[1][0])
+    assert np.array_equal(res[0][1], res[1][1])
