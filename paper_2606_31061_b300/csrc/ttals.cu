@@ -313,6 +313,7 @@ struct Impl final : ttals_stream {
   TC* Bhat[kMaxLevels] = {};           // B^_k, k = 1..k*-2 (also reconstruct temporaries)
   TC* E[kMaxLevels + 1] = {};          // E_k, k = 2..k*-1
   TC* part = nullptr;                  // split-K partials
+  TC* part2 = nullptr;                 // group sums of many split-K partials (orth, pass 0)
   TC* Y = nullptr;                     // reduced local-solve matrix of a level
   TC* Qa = nullptr;                    // first-pass orthogonal factor
   TC* Wpart = nullptr;            // per-CTA Gram partials (accumulation type TG = TC)
@@ -386,6 +387,9 @@ struct Impl final : ttals_stream {
   static constexpr int kMaxSplit = kF32State ? 1024 : 64;
   static constexpr int kTargetCtas = kF32State ? 8 * kSMs : 2 * kSMs;
   static constexpr long long kMinChunk = kF32State ? 4 * GB_K : GB_K;
+  // more than 2 kSplitGroup split partials of a local solve are first summed in groups of
+  // kSplitGroup by many threads (k_reduce_split_groups) before the Gram kernel's per-element sum
+  static constexpr int kSplitGroup = 16;
   GemmShape plan_solve(int k) const {      // Y = E_k B^_k^T
     return plan_gemm(rows(k), rk(k), rest[k], true, kMaxSplit, kTargetCtas, kMinChunk);
   }
@@ -419,6 +423,7 @@ struct Impl final : ttals_stream {
     cc_elems = std::max<size_t>(cc_elems, (size_t)kSMs * 4);
     TT_TRY(dalloc(&part, std::max<size_t>(part_elems, 1)));
     TT_TRY(dalloc(&Y, std::max<size_t>(y_elems, 1)));
+    TT_TRY(dalloc(&part2, std::max<size_t>((size_t)cdiv(kMaxSplit, kSplitGroup) * y_elems, 1)));
     TT_TRY(dalloc(&Qa, std::max<size_t>(y_elems, 1)));
     TT_TRY(dalloc(&Wpart, std::max<size_t>(wpart_elems, 1)));
     TT_TRY(dalloc(&T64, (size_t)kMaxRank * kMaxRank));
@@ -973,7 +978,18 @@ struct Impl final : ttals_stream {
       // already in Y) and leaves the reduced solve in Y
       const TC* src = pass == 0 ? (src0 ? src0 : (const TC*)part) : (const TC*)Qa;
       TC* dst = (pass + 1 == qr_passes) ? qout : Qa;
-      TT_TRY(launch_gen(k_gram<TC, TC, TG>, dim3(nblk), dim3(GRAM_THREADS), gsm, s, src, pass == 0 ? nsplit : 1,
+      int nsrc = pass == 0 ? nsplit : 1;
+      if (pass == 0 && !src0 && nsplit > 2 * kSplitGroup) {
+        const long long ne = n * r;
+        const int ng = (int)cdiv(nsplit, kSplitGroup);
+        const int nbr = (int)std::min<long long>(cdiv((long long)ng * ne, 256), 8 * kSMs);
+        TT_TRY(launch_gen(k_reduce_split_groups<TC>, dim3(nbr), dim3(256), 0, s, (const TC*)part, nsplit,
+                          kSplitGroup, ne, part2, (const Ctl*)ctl));
+        ++nlaunch;
+        src = part2;
+        nsrc = ng;
+      }
+      TT_TRY(launch_gen(k_gram<TC, TC, TG>, dim3(nblk), dim3(GRAM_THREADS), gsm, s, src, nsrc,
                         (long long)(n * r), (long long)n, r, (pass == 0 && !src0) ? Y : (TC*)nullptr, Wpart, (long long)rpb,
                         (const Ctl*)ctl));
       TT_TRY(launch_gen(k_factor<TC>, dim3(1), dim3(FACT_THREADS), fsm, s, (const TC*)Wpart, nblk, r,

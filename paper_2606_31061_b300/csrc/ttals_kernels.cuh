@@ -689,6 +689,38 @@ __global__ void __launch_bounds__(RED_THREADS) k_reduce_t(
   }
 }
 
+// First level of a split-K reduction for many splits: out[q][e] = the sum over the splits
+// s in [q G, min(nsplit, (q + 1) G)) of P[s][e], in split order (float-float pairs for FP32,
+// FP64 sums for FP64), one thread per (q, e): cdiv(nsplit, G) times the threads of a
+// per-element sum, for outputs too small to occupy the GPU otherwise.
+template <typename TC>
+__global__ void k_reduce_split_groups(const TC* __restrict__ P, int nsplit, int G, long long n,
+                                      TC* __restrict__ out, const Ctl* __restrict__ ctl) {
+  gen_pdl_start();
+  if (ctl && ctl->skip) return;
+  const int ng = (nsplit + G - 1) / G;
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < (long long)ng * n;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int q = (int)(t / n);
+    const long long e = t - (long long)q * n;
+    const int s1 = (q + 1) * G < nsplit ? (q + 1) * G : nsplit;
+    if constexpr (std::is_same<TC, float>::value) {
+      float h = 0.f, l = 0.f;
+      for (int s = q * G; s < s1; ++s) {
+        const float p = P[(long long)s * n + e];
+        const float u = h + p, bb = u - h;
+        l += (h - (u - bb)) + (p - bb);
+        h = u;
+      }
+      out[t] = h + l;
+    } else {
+      double v = 0.0;
+      for (int s = q * G; s < s1; ++s) v += Cvt<TC>::d(P[(long long)s * n + e]);
+      out[t] = from_acc<TC>(v);
+    }
+  }
+}
+
 // out = sum of nsplit partial matrices (n elements each, split stride n), in split order
 template <typename TC>
 __global__ void k_reduce_rows(const TC* __restrict__ P, int nsplit, long long n, TC* __restrict__ out,
