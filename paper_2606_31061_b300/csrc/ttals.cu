@@ -396,7 +396,8 @@ struct Impl final : ttals_stream {
   GemmShape plan_env(int k) const {        // E_{k+1}^T = E_k^T Q_k
     return plan_gemm((int)rest[k], rk(k), rows(k), true, kMaxSplit, kTargetCtas, kMinChunk);
   }
-  int gram_blocks(long long nrows) const { return (int)std::min<long long>(64, cdiv(nrows, 16)); }
+  // Gram partials of a level (the factor kernel sums them on one CTA): at most 16
+  int gram_blocks(long long nrows) const { return (int)std::min<long long>(16, cdiv(nrows, 16)); }
 
   ttals_status allocate() override {
     const bool f64 = std::is_same<TC, double>::value;

@@ -347,6 +347,29 @@ __global__ void __launch_bounds__(GRAM_THREADS) k_gram(
 constexpr int FACT_THREADS = 256;
 constexpr int kMaxRank = 64;
 
+// column c of R^{-1} for an upper triangular R (row i at R + i * ld, 1 / R_ii in rs), by back
+// substitution with the column in registers (RM >= r, compile time); written to Ti[i * r + c]
+template <int RM>
+__device__ __forceinline__ void tinv_column(const float* R, int ld, const float* rs, int r, int c, float* Ti) {
+  float t[RM];
+#pragma unroll
+  for (int i = 0; i < RM; ++i) t[i] = (i == c) ? rs[i < r ? i : 0] : 0.f;
+#pragma unroll
+  for (int i = RM - 2; i >= 0; --i) {
+    float s0 = 0.f, s1 = 0.f;
+#pragma unroll
+    for (int k = i + 1; k < RM; ++k) {
+      const float v = (k < r) ? R[i * ld + (k < r ? k : 0)] * t[k] : 0.f;
+      if ((k - i) & 1) s0 += v;
+      else s1 += v;
+    }
+    if (i < c) t[i] = -(s0 + s1) * rs[i < r ? i : 0];
+  }
+#pragma unroll
+  for (int i = 0; i < RM; ++i)
+    if (i < r) Ti[i * r + c] = t[i];
+}
+
 template <typename TW>
 __global__ void __launch_bounds__(FACT_THREADS) k_factor(
     const TW* __restrict__ Wpart, int nblk, int r, int mode, double* __restrict__ T64,
@@ -374,24 +397,38 @@ __global__ void __launch_bounds__(FACT_THREADS) k_factor(
   const int rr = r * r;
   if (tid == 0) bad = 0;
   __syncthreads();
+  // the upper triangle (i <= j), mirrored; each thread's loads of a batch of 8 partials are
+  // issued together, then summed in block order
   for (int e = tid; e < rr; e += blockDim.x) {
     const int i = e / r, j = e % r;
-    const int ii = i <= j ? i : j, jj = i <= j ? j : i;     // read the upper triangle
+    if (j < i) continue;
     double s = 0.0;
     if constexpr (std::is_same<TW, float>::value) {
       // float partials: float-float sum (TwoSum), one conversion at the end
       float h = 0.f, l = 0.f;
-      for (int b = 0; b < nblk; ++b) {
-        const float p = Wpart[(long long)b * rr + ii * r + jj];
-        const float t = h + p, bb = t - h;
-        l += (h - (t - bb)) + (p - bb);
-        h = t;
+      for (int b0 = 0; b0 < nblk; b0 += 8) {
+        float v[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) v[q] = b0 + q < nblk ? Wpart[(long long)(b0 + q) * rr + e] : 0.f;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const float t = h + v[q], bb = t - h;
+          l += (h - (t - bb)) + (v[q] - bb);
+          h = t;
+        }
       }
       s = (double)h + (double)l;
     } else {
-      for (int b = 0; b < nblk; ++b) s += Wpart[(long long)b * rr + ii * r + jj];
+      for (int b0 = 0; b0 < nblk; b0 += 8) {
+        double v[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) v[q] = b0 + q < nblk ? (double)Wpart[(long long)(b0 + q) * rr + e] : 0.0;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) s += v[q];
+      }
     }
     W[e] = s;
+    W[j * r + i] = s;
     if (!isfinite(s)) bad = 1;
   }
   __syncthreads();
@@ -448,10 +485,11 @@ __global__ void __launch_bounds__(FACT_THREADS) k_factor(
     asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(inv) : "f"(piv));
     inv = inv * fmaf(-piv, inv, 2.0f);
     if (tid == 0) rs[j] = rsqrtf(piv);
-    const int nt = r - j - 1;
-    for (int e = tid; e < nt * nt; e += blockDim.x) {
-      const int i = j + 1 + e / nt, k = j + 1 + e % nt;
-      if (k >= i) S[i * LD + k] = fmaf(-S[j * LD + i] * inv, S[j * LD + k], S[i * LD + k]);
+    // trailing update on a 16 x 16 thread grid (no integer division in the loop)
+    for (int i = j + 1 + (tid >> 4); i < r; i += FACT_THREADS / 16) {
+      const float sji = S[j * LD + i] * inv;
+      for (int k = j + 1 + (tid & 15); k < r; k += 16)
+        if (k >= i) S[i * LD + k] = fmaf(-sji, S[j * LD + k], S[i * LD + k]);
     }
     __syncthreads();
   }
@@ -461,22 +499,12 @@ __global__ void __launch_bounds__(FACT_THREADS) k_factor(
     if (k >= j) S[j * LD + k] *= rs[j];
   }
   __syncthreads();
-  // Tinv = R^{-1} (upper triangular), column-parallel back substitution, into W (as float)
+  // Tinv = R^{-1} (upper triangular), column-parallel back substitution, into W (as float):
+  // thread c keeps column c in registers (fully unrolled over the rank bound)
   float* Ti = reinterpret_cast<float*>(W);   // r x r, reuse
   if (tid < r) {
-    const int c = tid;
-    for (int i = 0; i < r; ++i) Ti[i * r + c] = 0.f;
-    Ti[c * r + c] = rs[c];
-    for (int i = c - 1; i >= 0; --i) {
-      float s0 = 0.f, s1 = 0.f;
-      int k = i + 1;
-      for (; k + 1 <= c; k += 2) {
-        s0 = fmaf(S[i * LD + k], Ti[k * r + c], s0);
-        s1 = fmaf(S[i * LD + k + 1], Ti[(k + 1) * r + c], s1);
-      }
-      if (k <= c) s0 = fmaf(S[i * LD + k], Ti[k * r + c], s0);
-      Ti[i * r + c] = -(s0 + s1) * rs[i];
-    }
+    if (r <= 32) tinv_column<32>(S, LD, rs, r, tid, Ti);
+    else tinv_column<kMaxRank>(S, LD, rs, r, tid, Ti);
   }
   __syncthreads();
   for (int e = tid; e < rr; e += blockDim.x) {
