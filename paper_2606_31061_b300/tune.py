@@ -22,7 +22,7 @@ only the order of FP32 sums.
 """
 from __future__ import annotations
 
-from typing import Dict, Optional, Sequence, Tuple
+from typing import Callable, Dict, Optional, Sequence, Tuple
 
 _CACHE: Dict[tuple, dict] = {}
 ENV_KINDS = (1, 2, 3, 4)
@@ -58,6 +58,38 @@ def _time_schedule(dims, ranks, n, ingest, sched, slices, steps) -> Optional[flo
         st.close()
 
 
+def coordinate_search(time_fn: Callable[[dict], Optional[float]]) -> Optional[dict]:
+    """The tuner's search, given a timing function (a schedule dict of KEYS -> ms per step, or
+    None where the schedule cannot run): every environment kind with the library's defaults,
+    every solve tile with the best kind, both factor clusters with the best of those; the
+    fastest of all timed candidates, with its time and every candidate's time.  None if no
+    candidate ran."""
+    results: Dict[Tuple[int, int, int, int], float] = {}
+
+    def trial(e, sk, ks, fc):
+        key4 = (e, sk, ks, fc)
+        if key4 not in results:
+            ms = time_fn(dict(zip(KEYS, key4)))
+            if ms is not None:
+                results[key4] = ms
+
+    for e in ENV_KINDS:
+        trial(e, 0, 0, 0)
+    if not results:
+        return None
+    e_best = min(results, key=results.get)[0]
+    for sk, ks in SOLVE_TILES:
+        trial(e_best, sk, ks, 0)
+    _, sk_best, ks_best, _ = min(results, key=results.get)
+    for fc in FACTOR_CLUSTERS:
+        trial(e_best, sk_best, ks_best, fc)
+    best4 = min(results, key=results.get)
+    best = dict(zip(KEYS, best4))
+    best["ms_per_step"] = results[best4]
+    best["tried"] = {f"env{a}_solve{b}_split{c}_fc{d}": round(v, 4) for (a, b, c, d), v in sorted(results.items())}
+    return best
+
+
 def best_schedule(dims: Sequence[int], ranks: Sequence[int], n: int, ingest: str = "f16",
                   steps: int = 8, seed: int = 1234) -> dict:
     """Fastest schedule for a batch of n streams of this shape (cached)."""
@@ -71,30 +103,9 @@ def best_schedule(dims: Sequence[int], ranks: Sequence[int], n: int, ingest: str
     shape = (2, n) + tuple(int(v) for v in dims)
     base = torch.randn(shape, generator=g, device="cuda", dtype=torch.float32)
     slices = (base * 16 + 128).clamp(0, 255).round().to(dt)
-    results: Dict[Tuple[int, int, int, int], float] = {}
-
-    def trial(e, sk, ks, fc):
-        key4 = (e, sk, ks, fc)
-        if key4 not in results:
-            ms = _time_schedule(dims, ranks, n, ingest, dict(zip(KEYS, key4)), slices, steps)
-            if ms is not None:
-                results[key4] = ms
-        return results.get(key4)
-
-    for e in ENV_KINDS:
-        trial(e, 0, 0, 0)
-    if not results:
+    best = coordinate_search(lambda sched: _time_schedule(dims, ranks, n, ingest, sched, slices, steps))
+    if best is None:
         _CACHE[key] = {}
         return {}
-    e_best = min(results, key=results.get)[0]
-    for sk, ks in SOLVE_TILES:
-        trial(e_best, sk, ks, 0)
-    _, sk_best, ks_best, _ = min(results, key=results.get)
-    for fc in FACTOR_CLUSTERS:
-        trial(e_best, sk_best, ks_best, fc)
-    best4 = min(results, key=results.get)
-    best = dict(zip(KEYS, best4))
-    best["ms_per_step"] = results[best4]
-    best["tried"] = {f"env{a}_solve{b}_split{c}_fc{d}": round(v, 4) for (a, b, c, d), v in sorted(results.items())}
     _CACHE[key] = best
     return best

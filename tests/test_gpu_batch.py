@@ -190,7 +190,9 @@ def test_batch_16_video_streams_full_size():
 
 
 @pytest.mark.parametrize("sched", [{"solve_kernel": 2, "factor_cluster": 4},
+                                   {"solve_kernel": 1, "k1_split": 1, "factor_cluster": 8},
                                    {"solve_kernel": 1, "k1_split": 2, "factor_cluster": 8},
+                                   {"solve_kernel": 1, "k1_split": 4, "factor_cluster": 4},
                                    {"env_kernel": 3, "solve_kernel": 2, "factor_cluster": 4},
                                    {"env_kernel": 4, "solve_kernel": 1, "k1_split": 8, "factor_cluster": 4}])
 def test_batch_schedules_agree(sched):
