@@ -347,29 +347,6 @@ __global__ void __launch_bounds__(GRAM_THREADS) k_gram(
 constexpr int FACT_THREADS = 256;
 constexpr int kMaxRank = 64;
 
-// column c of R^{-1} for an upper triangular R (row i at R + i * ld, 1 / R_ii in rs), by back
-// substitution with the column in registers (RM >= r, compile time); written to Ti[i * r + c]
-template <int RM>
-__device__ __forceinline__ void tinv_column(const float* R, int ld, const float* rs, int r, int c, float* Ti) {
-  float t[RM];
-#pragma unroll
-  for (int i = 0; i < RM; ++i) t[i] = (i == c) ? rs[i < r ? i : 0] : 0.f;
-#pragma unroll
-  for (int i = RM - 2; i >= 0; --i) {
-    float s0 = 0.f, s1 = 0.f;
-#pragma unroll
-    for (int k = i + 1; k < RM; ++k) {
-      const float v = (k < r) ? R[i * ld + (k < r ? k : 0)] * t[k] : 0.f;
-      if ((k - i) & 1) s0 += v;
-      else s1 += v;
-    }
-    if (i < c) t[i] = -(s0 + s1) * rs[i < r ? i : 0];
-  }
-#pragma unroll
-  for (int i = 0; i < RM; ++i)
-    if (i < r) Ti[i * r + c] = t[i];
-}
-
 template <typename TW>
 __global__ void __launch_bounds__(FACT_THREADS) k_factor(
     const TW* __restrict__ Wpart, int nblk, int r, int mode, double* __restrict__ T64,
@@ -471,10 +448,15 @@ __global__ void __launch_bounds__(FACT_THREADS) k_factor(
     S[i * LD + j] = (float)(W[e] * dsc[i] * dsc[j]);
   }
   __syncthreads();
-  // right-looking elimination with one barrier per pivot: row j stays unscaled (d_j times the
-  // unit factor's row) until every pivot is done; the pivot's reciprocal is the hardware
-  // approximation refined by one Newton step (about 1e-7 relative)
-  __shared__ float rs[kMaxRank];                // 1 / sqrt(pivot j) = 1 / R_jj
+  // right-looking LDL^T elimination with one barrier per pivot (S's rows keep the unscaled
+  // pivot rows); the pivot's reciprocal is the hardware approximation refined by one Newton
+  // step (about 1e-7 relative).  The same row operations applied to the identity build the
+  // unit lower factor's inverse Li = L_u^{-1} alongside, so that with S = L_u D_p L_u^T and
+  // R = D_p^{1/2} L_u^T (R^T R = D W D): T = D R^{-1} = D L_u^{-T} D_p^{-1/2}.
+  __shared__ float rs[kMaxRank];                // 1 / sqrt(pivot j)
+  float* Li = reinterpret_cast<float*>(W);      // r x r (W is not needed any more)
+  for (int e = tid; e < rr; e += blockDim.x) Li[e] = (e / r == e % r) ? 1.f : 0.f;
+  __syncthreads();
   for (int j = 0; j < r; ++j) {
     const float piv = S[j * LD + j];
     if (!(piv > 1e-4f)) {            // uniform: every thread reads the same value
@@ -485,31 +467,20 @@ __global__ void __launch_bounds__(FACT_THREADS) k_factor(
     asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(inv) : "f"(piv));
     inv = inv * fmaf(-piv, inv, 2.0f);
     if (tid == 0) rs[j] = rsqrtf(piv);
-    // trailing update on a 16 x 16 thread grid (no integer division in the loop)
+    // on a 16 x 16 thread grid (no integer division in the loops): the trailing update of S
+    // (rows i > j, columns k >= i) and the inverse rows i > j (columns c <= j)
     for (int i = j + 1 + (tid >> 4); i < r; i += FACT_THREADS / 16) {
       const float sji = S[j * LD + i] * inv;
       for (int k = j + 1 + (tid & 15); k < r; k += 16)
         if (k >= i) S[i * LD + k] = fmaf(-sji, S[j * LD + k], S[i * LD + k]);
+      for (int c = tid & 15; c <= j; c += 16) Li[i * r + c] = fmaf(-sji, Li[j * r + c], Li[i * r + c]);
     }
     __syncthreads();
   }
-  // R = the rows scaled by 1 / sqrt(pivot): R^T R = D W D
+  // T[k][i] = dsc_k Li[i][k] rs_i (upper triangular)
   for (int e = tid; e < rr; e += blockDim.x) {
-    const int j = e / r, k = e % r;
-    if (k >= j) S[j * LD + k] *= rs[j];
-  }
-  __syncthreads();
-  // Tinv = R^{-1} (upper triangular), column-parallel back substitution, into W (as float):
-  // thread c keeps column c in registers (fully unrolled over the rank bound)
-  float* Ti = reinterpret_cast<float*>(W);   // r x r, reuse
-  if (tid < r) {
-    if (r <= 32) tinv_column<32>(S, LD, rs, r, tid, Ti);
-    else tinv_column<kMaxRank>(S, LD, rs, r, tid, Ti);
-  }
-  __syncthreads();
-  for (int e = tid; e < rr; e += blockDim.x) {
-    const int i = e / r;
-    const double t = dsc[i] * (double)Ti[e];
+    const int k = e / r, i = e % r;
+    const double t = i >= k ? dsc[k] * (double)(Li[i * r + k] * rs[i]) : 0.0;
     T64[e] = t;
     T32[e] = (float)t;
   }
