@@ -901,13 +901,15 @@ __global__ void __launch_bounds__(K1T_THREADS, 1)
 // of Y.
 //  1. W1 = Y^T Y: every rank sums the solve kernel's row-tile Gram partials in tile order
 //     (float-float) while its rows of Y are still arriving.
-//  2. Every rank factors the scaled Gram D W1 D = L L^T (FP32, one warp).
+//  2. Every rank factors the scaled Gram D W1 D = L L^T: in FP64 (r64::ldl_factor, the
+//     default) or in FP32 (one warp).
 //  3. Q1 = Y D L^{-T}: each thread forward-substitutes whole rows, z = L^{-1} (D y),
 //     and rounds them to the ingest type (the values that multiply X in the env kernel).
 //  4. W2 partial = (my rounded rows)^T (my rounded rows) on tensor cores (exact products),
 //     written to global memory; the environment kernel sums the partials in rank order.
-// A failed factorisation (scaled pivot <= 1e-4: rank-deficient or badly conditioned Y)
-// takes the FP64 Householder QR of Y on rank 0 instead.
+// A failed factorisation (scaled pivot <= 1e-4: an ill-conditioned local solve) takes an
+// FP64-accurate Cholesky-QR instead (float-float Gram of Y, FP64 factor, float-float apply);
+// only a pivot at FP64 rounding takes the FP64 Householder QR of Y on rank 0.
 constexpr int K1B_THREADS = 256;
 constexpr int KB_CLUSTER = 8;       // the largest factor cluster: W2-partial slab stride
 // static shared memory of k_fast_factor (W1 as float + its rounding error, L^T, the FP64
