@@ -851,10 +851,23 @@ def run_reference(args, rank):
 
 
 def profile_case(args):
-    """Untimed pushes for a profiler capture: one video stream (profile_case = "single") or a
-    batch of args.batch video streams ("batched"), args.warmup + args.steps pushes."""
+    """Untimed pushes for a profiler capture: one video stream (profile_case = "single"), a
+    batch of args.batch video streams ("batched"), or one sensor-shaped stream in FP32 on the
+    generic path ("sensor"), args.warmup + args.steps pushes."""
     import torch
     from paper_2606_31061_b300.ttals import Stream
+    if args.profile_case == "sensor":
+        from paper_2606_31061_b300 import synth
+        sp = synth.make_stream("sensor")
+        pool = to_device(np.stack([synth.round_to_ingest(x, "f32")[0] for x in sp.take(4)]), "f32")
+        st = Stream(SENSOR_DIMS, SENSOR_RANKS, ingest="f32")
+        h = torch.cuda.current_stream().cuda_stream
+        for t in range(args.warmup + args.steps):
+            st.push_ptr(pool[t % 4].data_ptr(), h)
+        torch.cuda.synchronize()
+        st.sync()
+        st.close()
+        return
     S = args.batch if args.profile_case == "batched" else 0
     pool = to_device(make_pool(args.ingest, max(8, S + 4)), args.ingest)
     st = Stream(DIMS, RANKS, ingest=args.ingest, n_streams=S)
@@ -889,9 +902,10 @@ def main():
     ap.add_argument("--ablation", type=int, default=1, help="Sec. 5.4 orthogonality ablation arm (0: skip)")
     ap.add_argument("--oracle-frames", type=int, default=40,
                     help="prefix on which the oracle is timed and compared with the GPU path")
-    ap.add_argument("--profile-case", default=None, choices=["single", "batched"],
-                    help="for profilers: run --warmup + --steps pushes of one video stream, or of a "
-                         "batch of --batch video streams, untimed, and print no bench line")
+    ap.add_argument("--profile-case", default=None, choices=["single", "batched", "sensor"],
+                    help="for profilers: run --warmup + --steps pushes of one video stream, of a "
+                         "batch of --batch video streams, or of one FP32 sensor-shaped stream, untimed, "
+                         "and print no bench line")
     args = ap.parse_args()
     rank = env_int("RANK", 0)
     world = env_int("WORLD_SIZE", 1)
